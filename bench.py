@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput and time-to-accuracy of asynchronous Sparse SAGA (ASAGA) on GB300.
+
+One step = one epoch of asynchronous Sparse SAGA updates (n sampled rows,
+Algorithm 2) followed by the segment boundary: the float64 objective and the
+stopping test (plus the float64 abar recomputation every 5th step).  The
+metric is epochs/s on the RCV1-shaped l2-logistic workload (n=700000,
+d=47000, ~75 nnz per row with Zipf(1.1) columns, fp32 values, lambda=1/n,
+gamma=1/(3L)), with the problem resident in HBM.  The line also reports:
+  time_to_target  seconds from x=0 to 1e-6 relative suboptimality against
+                  the float64 f* stored in tests/golden;
+  e2e             the same epochs/s through the public C ABI from pinned host
+                  buffers, every step copying the problem in and the iterate
+                  out (asaga_create -> asaga_run(1 epoch) -> asaga_get_state
+                  -> asaga_destroy);
+  roofline        algorithmic HBM bytes of the update kernel per launch over
+                  its CUDA-event time, against the measured HBM peak;
+  cpu_baseline    the float64 CPU checker on a bounded sample, one host core.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank solves its own replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1606_04809_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "rcv1like": dict(make=synth.rcv1_like, golden="fstar_rcv1like.json",
+                     desc="l2-logistic, RCV1-shaped synthetic: n=700000, d=47000, ~75 nnz/row (4..1224, "
+                          "lognormal), Zipf(1.1) columns, |N(0,1)| row-normalised, fp32 values, lambda=1/n, "
+                          "gamma=1/(3L)"),
+    "covtypelike": dict(make=synth.covtype_like, golden="fstar_covtypelike.json",
+                        desc="ridge, Covtype-shaped synthetic: n=581000, d=54 dense, N(0,1) standardised, fp16 "
+                             "values, lambda=1e-3, gamma=1/(3L)"),
+    "urllike": dict(make=synth.url_like, golden="fstar_urllike.json",
+                    desc="l2-logistic, URL-shaped synthetic: n=2400000, d=3200000, ~115 nnz/row (16..414), "
+                         "Zipf(1.1) columns, binary row-normalised, bf16 values, lambda=1/n, gamma=1/(3L)"),
+}
+ABAR_EVERY = 5
+TARGET = 1e-6
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rcv1like", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_golden(name, p):
+    path = os.path.join(ROOT, "tests", "golden", name)
+    if not os.path.exists(path):
+        return None, "no stored f*"
+    g = json.load(open(path))
+    fp, want = p.fingerprint(), g["fingerprint"]
+    same = (fp["structure_sha256"] == want["structure_sha256"]
+            and abs(fp["sum_values"] - want["sum_values"]) <= 1e-9 * abs(want["sum_values"])
+            and abs(fp["sum_labels"] - want["sum_labels"]) <= 1e-9 * max(1.0, abs(want["sum_labels"])))
+    if not same:
+        return None, "regenerated problem differs from the one f* was computed for"
+    return g, None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            return float(json.load(open(path))["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(workload):
+    """Per-launch DRAM bytes of the update kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"update_kernel_{workload}.md")
+    src = os.path.join(ROOT, "paper_1606_04809_gb300", "csrc", "update.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    kv = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("update.cu sha256") != sha:
+        return None
+    try:
+        return int(float(kv["traffic_bytes_per_launch"]))
+    except Exception:
+        return None
+
+
+def update_hbm_bytes(p, storage):
+    """Algorithmic HBM bytes of one epoch of updates: each sampled row reads
+    its CSR slice (4 B index + value) once, row_ptr (2 x 8 B), its label
+    (4 B) and swaps alpha_i (4 B read + 4 B write).  The per-column state is
+    L2-resident by design and not counted."""
+    vsz = {"f32": 4, "bf16": 2, "f16": 2}[storage]
+    per_nnz = vsz + (0 if p.dense else 4)
+    per_row = (0 if p.dense else 16) + 4 + 8
+    return p.nnz * per_nnz + p.n * per_row
+
+
+# ---------------------------------------------------------------- reference arm
+
+def time_checker(p, seconds, steps=None, warmup=0):
+    """Float64 CPU checker: one step = one epoch of serial Sparse SAGA + the
+    float64 objective.  Runs `steps` steps, or as many as fit in `seconds`."""
+    from oracle import reference as R
+    L = R.lipschitz(p)
+    gamma, D = 1.0 / (3.0 * L), R.reweighting(p)
+    st = R.State.zeros(p)
+
+    def step(k):
+        R.sparse_saga(p, st, synth.sample_indices(p.n, p.n, 30, k + 1), gamma, D)
+        return R.objective(p, st.x)
+
+    for k in range(warmup):
+        step(k)
+    t0, done = time.perf_counter(), 0
+    while True:
+        step(warmup + done)
+        done += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and done >= steps) or (steps is None and el >= seconds):
+            break
+    return done / el, done, el
+
+
+def run_reference(args, p, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    eps, done, el = time_checker(p, args.cpu_seconds, steps=args.steps, warmup=min(args.warmup, 1))
+    line = {
+        "impl": "reference", "metric": "epochs/s", "value": eps, "unit": "epochs/s", "n_gpus": args.gpus,
+        "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["desc"]},
+        "cpu_baseline": {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0"},
+        "e2e": {"value": eps, "unit": "epochs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    wl = WORKLOADS[args.workload]
+    p = wl["make"]()
+    if args.impl == "reference":
+        return run_reference(args, p, wl)
+
+    import torch
+    from paper_1606_04809_gb300 import asaga
+    from paper_1606_04809_gb300 import build as lib_build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib_build.build()
+    asaga.load()
+    stream = torch.cuda.current_stream()
+    storage = p.storage if p.storage != "f64" else "f32"
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    opts = dict(seed=1000 + rank, abar_recompute_every=ABAR_EVERY, cuda_stream=stream.cuda_stream)
+    ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
+    info = asaga.asaga_get_info(ctx.ctx)
+
+    for _ in range(args.warmup):
+        asaga.asaga_run(ctx.ctx, 1)
+    barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    solver_s, launches, f_last = 0.0, 0, None
+    e0.record(stream)
+    for _ in range(args.steps):
+        s, r = asaga.asaga_run(ctx.ctx, 1)
+        solver_s += r.solver_seconds
+        launches += r.kernel_launches
+        f_last = r.f_last
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    ctx.close()
+
+    value = world * args.steps / (ms * 1e-3)
+    upd_ms = 1e3 * solver_s / args.steps
+    hbm_bytes = update_hbm_bytes(p, storage)
+    peak, peak_kind = measured_peak_hbm()
+    achieved = hbm_bytes / (upd_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(args.workload), "kernel": "update_kernel (one launch = one epoch)",
+                "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": upd_ms, "peak_source": peak_kind}
+
+    # time to 1e-6 from x = 0
+    ttt = None
+    golden, why = load_golden(wl["golden"], p)
+    if not args.no_ttt:
+        if golden is None:
+            ttt = {"status": "skipped", "reason": why}
+        else:
+            with asaga.Context(p, storage=storage, **opts) as c2:
+                s, r = asaga.asaga_run(c2.ctx, 200, TARGET, golden["fstar"])
+            ttt = {"target_rel_subopt": TARGET, "status": asaga.STATUS_NAMES[s], "epochs": r.epochs,
+                   "seconds_wall": r.seconds, "seconds_device": r.solver_seconds + r.eval_seconds,
+                   "solver_seconds": r.solver_seconds, "eval_seconds": r.eval_seconds,
+                   "rel_subopt": r.rel_subopt, "fstar": golden["fstar"], "fstar_bound": golden["bound"]}
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        rp = torch.from_numpy(np.ascontiguousarray(p.row_ptr, dtype=np.int64)).pin_memory() if not p.dense else None
+        ci = torch.from_numpy(np.ascontiguousarray(p.col_idx, dtype=np.int32)).pin_memory() if not p.dense else None
+        npdt = {"f32": np.float32, "f16": np.float16}
+        if storage == "bf16":
+            v32 = np.ascontiguousarray(p.values, dtype=np.float32).view(np.uint32)
+            vals = torch.from_numpy((v32 >> 16).astype(np.uint16).view(np.int16)).pin_memory()
+        else:
+            vals = torch.from_numpy(np.ascontiguousarray(p.values, dtype=npdt[storage])).pin_memory()
+        lab = torch.from_numpy(np.ascontiguousarray(p.labels, dtype=np.float64)).pin_memory()
+        prob = asaga.Problem(p.n, p.d, rp, ci, vals, storage, lab, dense=p.dense)
+        xh = torch.empty(p.d, dtype=torch.float32).pin_memory()
+        o = asaga.asaga_default_options(loss=p.loss, lam=p.lam, storage_dtype=storage, **opts)
+        h2d = sum(t.numel() * t.element_size() for t in (rp, ci, vals, lab) if t is not None)
+        d2h = p.d * 4 + 8
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            c = asaga.asaga_create(prob, o)
+            asaga.asaga_run(c, 1)
+            asaga.load().asaga_get_state(c, xh.data_ptr(), None, None)
+            asaga.asaga_destroy(c)
+        el = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * args.e2e_steps / el, "unit": "epochs/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+               "step": "asaga_create(pinned host CSR) + asaga_run(1 epoch) + asaga_get_state(x) + asaga_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        eps, done, el = time_checker(p, args.cpu_seconds)
+        cpu = {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0 ({el:.1f} s)"}
+
+    a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
+    if rank == 0:
+        line = {
+            "metric": "epochs/s", "value": value, "unit": "epochs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
+                       "warps": info["warps"], "gamma": info["gamma"], "abar_recompute_every": ABAR_EVERY,
+                       "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "time_to_target": ttt,
+            "e2e": e2e,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "f_last": f_last,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,220 @@
+/*
+ * asaga.h -- C ABI of a GB300 (sm_103a) solver for lock-free asynchronous
+ * Sparse SAGA (ASAGA; Leblond, Pedregosa, Lacoste-Julien, arXiv:1606.04809).
+ *
+ * Problem (Eq. finiteSum with the model of Sec. 4.1):
+ *     min_x f(x) = 1/n sum_i phi_i(a_i . x) + lambda/2 |x|^2,
+ *     logistic phi_i(z) = log(1 + exp(-b_i z)), b_i in {-1,+1},
+ *     squared  phi_i(z) = (z - y_i)^2 / 2.
+ * Update (Eq. SparseSAGA with the projected l2 term of Sec. 4.2, run as in
+ * Algorithm 2): for a uniformly sampled row i with support S_i,
+ *     delta = phi'_i(a_i . x^) - alpha_i,
+ *     x_v   -= gamma (delta a_iv + D_v abar_v + lambda D_v x^_v),  v in S_i,
+ *     abar_v += delta a_iv / n,                                   v in S_i,
+ *     alpha_i = phi'_i(a_i . x^),
+ * where x^ is the (inconsistent) value read for the dot product and
+ * D_v = n / |{i : v in S_i}| (Sec. 2), 0 for columns that no row touches.
+ * Many GPU warps run this update concurrently without locks; the adds to x
+ * and abar are atomic (Sec. 3.2, Property "atomicity").
+ *
+ * Conventions for every entry point:
+ *   - the library owns all device state; it copies the problem at create
+ *     time and never keeps a caller pointer after a call returns;
+ *   - every call returns an asaga_status and never aborts the process;
+ *     asaga_last_error() gives a one-line reason for the last failure;
+ *   - host pointers are plain CPU memory (pinned or not); "device" pointers
+ *     are CUDA global-memory addresses on the current device;
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef ASAGA_H
+#define ASAGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque solver context (one problem, its device copy and the solver state). */
+typedef struct asaga_ctx asaga_ctx;
+
+typedef enum {
+    ASAGA_OK = 0,
+    ASAGA_EINVAL = 1,         /* invalid argument or problem; nothing changed  */
+    ASAGA_ENOMEM = 2,         /* a device allocation failed                    */
+    ASAGA_ECUDA = 3,          /* a CUDA call failed (no GPU, launch error, ...) */
+    ASAGA_ETIMEOUT = 4,       /* the run stopped at options.timeout_s          */
+    ASAGA_EDIVERGED = 5,      /* objective or iterate became non-finite        */
+    ASAGA_ENOTCONVERGED = 6   /* max_epochs reached before the target          */
+} asaga_status;
+
+typedef enum { ASAGA_LOSS_LOGISTIC = 0, ASAGA_LOSS_SQUARED = 1 } asaga_loss;
+
+typedef enum { ASAGA_F64 = 0, ASAGA_F32 = 1, ASAGA_BF16 = 2, ASAGA_F16 = 3 } asaga_dtype;
+
+/*
+ * The data matrix A (n rows a_i, d columns) in CSR form, and the labels.
+ *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz;
+ *   col_idx  int32[nnz], each in [0, d), distinct within a row (any order);
+ *   values   nnz numbers of type values_dtype (F64, F32, BF16 or F16), finite;
+ *   labels   float64[n]: +1/-1 for logistic, finite targets for squared.
+ * The support S_i of row i is its stored pattern (an explicitly stored 0
+ * counts as support).  dense = 1 means values holds n*d numbers row-major
+ * and row_ptr/col_idx are NULL.  on_device = 1 means all four arrays are
+ * device pointers; they are read only during asaga_create.
+ */
+typedef struct {
+    int64_t n, d, nnz;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const void *values;
+    asaga_dtype values_dtype;
+    const double *labels;
+    int dense;
+    int on_device;
+} asaga_problem;
+
+/*
+ * Solver options; asaga_default_options() fills every field.
+ *   loss                 the phi_i above.
+ *   lambda               l2 weight, >= 0 (the paper uses 1/n, Sec. 4.2).
+ *   gamma                step size; <= 0 picks 1/(3L), L = c max_i |a_i|^2 +
+ *                        lambda with c = 1/4 (logistic) or 1 (squared).
+ *   storage_dtype        device type of A's values: F32, BF16 or F16 (the
+ *                        iterate, memory and dot products are always F32).
+ *   max_warps            concurrent solver warps ("cores"); 0 = automatic
+ *                        (a bound derived from n keeps the overlap well below
+ *                        n/10, the condition of Theorem 2).
+ *   deterministic        1 = one warp processes the updates strictly in
+ *                        order (bitwise reproducible; parity mode).
+ *   seed                 seed of the row sampler (counter-based SplitMix64).
+ *   epochs_per_segment   epochs between float64 objective evaluations.
+ *   abar_recompute_every segments between float64 recomputations of abar
+ *                        from the memory (0 = never).
+ *   timeout_s            wall-clock limit of one asaga_run (0 = none).
+ *   cuda_stream          cudaStream_t to run on; NULL = a stream the library
+ *                        creates.  All work of a context is ordered on it.
+ *   column_stride        spacing of the per-column state in 16-byte units
+ *                        (1 = packed; 8 = one 128-byte line per column, which
+ *                        spreads atomics on very small d); 0 = automatic.
+ */
+typedef struct {
+    asaga_loss loss;
+    double lambda;
+    double gamma;
+    asaga_dtype storage_dtype;
+    int max_warps;
+    int deterministic;
+    uint64_t seed;
+    int epochs_per_segment;
+    int abar_recompute_every;
+    double timeout_s;
+    void *cuda_stream;
+    int column_stride;
+} asaga_options;
+
+/* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and
+ * eval_seconds split the device time (CUDA events) between the update kernel
+ * and the float64 evaluations.  abar_drift = max_v |abar_v - (1/n) sum_i
+ * alpha_i a_iv| seen at the last recomputation (0 if none ran). */
+typedef struct {
+    double epochs;
+    double seconds;
+    double solver_seconds;
+    double eval_seconds;
+    double f_last;
+    double rel_subopt;
+    int64_t updates;
+    double abar_drift;
+    int64_t segments;
+    int64_t kernel_launches;
+} asaga_result;
+
+/* Static facts about a context. */
+typedef struct {
+    int64_t n, d, nnz;
+    double L;            /* c max_i |a_i|^2 + lambda, on the stored values      */
+    double gamma;        /* step size in use                                    */
+    double delta;        /* max_v |{i : v in S_i}| / n (Sec. 3.3, "Sparsity")   */
+    int warps;           /* concurrent solver warps of asaga_run                */
+    int column_stride;   /* per-column state spacing in 16-byte units           */
+    int64_t device_bytes;/* device memory held by the context                   */
+    int64_t max_row_len; /* longest row                                          */
+} asaga_info;
+
+/* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
+ * automatic warps, asynchronous, seed 0, 1 epoch per segment, no abar
+ * recomputation, no timeout, own stream, automatic column stride. */
+void asaga_default_options(asaga_options *opt);
+
+/* Validates the problem, copies it to the device in options->storage_dtype,
+ * computes D, L and gamma, and zeroes x, alpha and abar (Sec. 2: x0 = 0,
+ * alpha0 = 0).  On success *out owns the context (free with asaga_destroy).
+ * EINVAL: NULL pointer, n or d < 1, nnz < 0, malformed CSR (row_ptr not
+ * monotone, column out of range or repeated in a row), non-finite value or
+ * label, logistic label not +-1, lambda < 0 or non-finite, unsupported dtype.
+ * ECUDA / ENOMEM: no usable GPU or not enough device memory. */
+asaga_status asaga_create(asaga_ctx **out, const asaga_problem *problem,
+                          const asaga_options *options);
+
+/* Runs asynchronous Sparse SAGA (Algorithm 2) in segments of
+ * options.epochs_per_segment epochs (an epoch is n updates), evaluating f in
+ * float64 after each segment.  Stops when target_rel_subopt > 0 and
+ * (f - f_star) / |f_star| <= target_rel_subopt (returns OK), or after
+ * max_epochs (returns OK if target_rel_subopt <= 0, else ENOTCONVERGED).
+ * Continues from the current state; the sampler stream continues too.
+ * EDIVERGED if f turns non-finite; ETIMEOUT at options.timeout_s.
+ * res may be NULL. */
+asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subopt,
+                       double f_star, asaga_result *res);
+
+/* Deterministic replay: runs one update per entry of idx (row indices in
+ * [0,n)), strictly in order, on a single warp.  idx is a host pointer if
+ * idx_on_device = 0, else a device pointer.  This is the serial Sparse SAGA
+ * iteration in float32 and matches a float64 serial run on the same index
+ * sequence to rounding.  EINVAL on an index out of range (checked on the
+ * host for host input; on the device otherwise, with no update applied
+ * past the bad entry). */
+asaga_status asaga_run_indices(asaga_ctx *ctx, const int64_t *idx, int64_t count,
+                               int idx_on_device);
+
+/* f(x) at the current iterate, computed on the GPU in float64 (float32 x and
+ * stored values widened exactly). */
+asaga_status asaga_objective(asaga_ctx *ctx, double *f);
+
+/* grad f(x) = 1/n A^T phi'(A x) + lambda x in float64 on the GPU.  If grad is
+ * not NULL it receives d float64 values (host memory); norm2 (may be NULL)
+ * receives |grad f(x)|^2. */
+asaga_status asaga_full_grad(asaga_ctx *ctx, double *grad, double *norm2);
+
+/* Recomputes abar = (1/n) sum_i alpha_i a_i from the memory with float64
+ * accumulation (cancelling the float32 drift of the running sums) and stores
+ * it.  drift (may be NULL) receives max_v |abar_v(before) - abar_v(exact)|. */
+asaga_status asaga_recompute_abar(asaga_ctx *ctx, double *drift);
+
+/* Copies the state to host memory: x and abar (d floats each), alpha (n
+ * floats).  Any pointer may be NULL. */
+asaga_status asaga_get_state(asaga_ctx *ctx, float *x, float *abar, float *alpha);
+
+/* Overwrites the state from host memory (checkpoint restore); any pointer may
+ * be NULL to keep that part.  The sampler position is set to updates_done. */
+asaga_status asaga_set_state(asaga_ctx *ctx, const float *x, const float *abar,
+                             const float *alpha, int64_t updates_done);
+
+asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
+
+/* Reason for the last failure of a call on ctx (or of asaga_create when ctx
+ * is NULL); never NULL. */
+const char *asaga_last_error(const asaga_ctx *ctx);
+
+const char *asaga_status_string(asaga_status s);
+
+/* Frees the context and its device memory; NULL is a no-op. */
+void asaga_destroy(asaga_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASAGA_H */

@@ -1,0 +1,290 @@
+"""Python binding of the C ABI in include/asaga.h (ctypes; argument
+marshalling only -- every step of the solver runs in the CUDA library).
+
+The functions carry the C names.  Host arrays are numpy arrays; device
+arrays may be passed as torch CUDA tensors (their data pointers are used).
+Calls that fail with ASAGA_EINVAL / ENOMEM / ECUDA raise AsagaError;
+asaga_run returns its status, since ENOTCONVERGED, ETIMEOUT and EDIVERGED
+are outcomes of a run rather than misuse.  Loading fails loudly when the
+library has not been built: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libasaga.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "asaga.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDIVERGED, ENOTCONVERGED = range(7)
+STATUS_NAMES = ["ASAGA_OK", "ASAGA_EINVAL", "ASAGA_ENOMEM", "ASAGA_ECUDA", "ASAGA_ETIMEOUT",
+                "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED"]
+LOSS = {"logistic": 0, "squared": 1}
+DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+
+
+class AsagaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 7 else status}: {message}")
+        self.status = status
+        self.message = message
+
+
+class asaga_problem(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("values", ctypes.c_void_p),
+                ("values_dtype", ctypes.c_int), ("labels", ctypes.c_void_p), ("dense", ctypes.c_int),
+                ("on_device", ctypes.c_int)]
+
+
+class asaga_options(ctypes.Structure):
+    _fields_ = [("loss", ctypes.c_int), ("lambda_", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("storage_dtype", ctypes.c_int), ("max_warps", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("epochs_per_segment", ctypes.c_int),
+                ("abar_recompute_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int)]
+
+
+class asaga_result(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_double), ("seconds", ctypes.c_double), ("solver_seconds", ctypes.c_double),
+                ("eval_seconds", ctypes.c_double), ("f_last", ctypes.c_double), ("rel_subopt", ctypes.c_double),
+                ("updates", ctypes.c_int64), ("abar_drift", ctypes.c_double), ("segments", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class asaga_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64), ("L", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("warps", ctypes.c_int),
+                ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
+                ("max_row_len", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def header_functions() -> list:
+    """Names of the functions include/asaga.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(asaga_[a-z_]+)\s*\(", text)))
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Loads libasaga.so (built by paper_1606_04809_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libasaga.so not built ({path}); run paper_1606_04809_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, vp, i64, i32, dbl = ctypes.POINTER, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.asaga_default_options.argtypes = [P(asaga_options)]
+    L.asaga_default_options.restype = None
+    L.asaga_create.argtypes = [P(vp), P(asaga_problem), P(asaga_options)]
+    L.asaga_run.argtypes = [vp, dbl, dbl, dbl, P(asaga_result)]
+    L.asaga_run_indices.argtypes = [vp, vp, i64, i32]
+    L.asaga_objective.argtypes = [vp, P(dbl)]
+    L.asaga_full_grad.argtypes = [vp, vp, P(dbl)]
+    L.asaga_recompute_abar.argtypes = [vp, P(dbl)]
+    L.asaga_get_state.argtypes = [vp, vp, vp, vp]
+    L.asaga_set_state.argtypes = [vp, vp, vp, vp, i64]
+    L.asaga_get_info.argtypes = [vp, P(asaga_info)]
+    L.asaga_last_error.argtypes = [vp]
+    L.asaga_last_error.restype = ctypes.c_char_p
+    L.asaga_status_string.argtypes = [i32]
+    L.asaga_status_string.restype = ctypes.c_char_p
+    L.asaga_destroy.argtypes = [vp]
+    L.asaga_destroy.restype = None
+    for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_objective", "asaga_full_grad",
+              "asaga_recompute_abar", "asaga_get_state", "asaga_set_state", "asaga_get_info"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):  # torch tensor
+        assert a.is_contiguous()
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(type(a))
+
+
+def _check(ctx, status: int):
+    if status != OK:
+        raise AsagaError(status, asaga_last_error(ctx))
+
+
+# --------------------------------------------------------------------- calls
+
+def asaga_default_options(**overrides) -> asaga_options:
+    o = asaga_options()
+    load().asaga_default_options(ctypes.byref(o))
+    for k, v in overrides.items():
+        if k == "lam" or k == "lambda":
+            k = "lambda_"
+        if k == "loss" and isinstance(v, str):
+            v = LOSS[v]
+        if k == "storage_dtype" and isinstance(v, str):
+            v = DTYPE[v]
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Problem:
+    """Holds the arrays of an asaga_problem alive while the struct is in use."""
+
+    def __init__(self, n, d, row_ptr, col_idx, values, values_dtype, labels, dense=False, on_device=False,
+                 nnz=None):
+        self.keep = (row_ptr, col_idx, values, labels)
+        self.struct = asaga_problem(
+            n=n, d=d, nnz=(int(nnz) if nnz is not None else (0 if dense else int(len(col_idx)))),
+            row_ptr=_ptr(row_ptr), col_idx=_ptr(col_idx), values=_ptr(values),
+            values_dtype=DTYPE[values_dtype] if isinstance(values_dtype, str) else values_dtype,
+            labels=_ptr(labels), dense=int(dense), on_device=int(on_device))
+
+
+def host_problem(p, values_dtype: str = "f64") -> Problem:
+    """asaga_problem over the host arrays of a generated problem (values sent
+    as float64 by default; the library rounds them to the storage type)."""
+    np_dt = {"f64": np.float64, "f32": np.float32, "f16": np.float16}
+    if values_dtype == "bf16":  # values already on the bf16 grid: keep the top 16 bits
+        v32 = np.ascontiguousarray(p.values, dtype=np.float32).view(np.uint32)
+        if np.any(v32 & 0xFFFF):
+            raise ValueError("values are not exactly representable in bf16")
+        vals = (v32 >> 16).astype(np.uint16)
+    else:
+        vals = np.ascontiguousarray(p.values, dtype=np_dt[values_dtype])
+    labels = np.ascontiguousarray(p.labels, dtype=np.float64)
+    if p.dense:
+        return Problem(p.n, p.d, None, None, vals, values_dtype, labels, dense=True)
+    return Problem(p.n, p.d, np.ascontiguousarray(p.row_ptr, dtype=np.int64),
+                   np.ascontiguousarray(p.col_idx, dtype=np.int32), vals, values_dtype, labels)
+
+
+def asaga_create(problem: Problem, options: asaga_options) -> int:
+    ctx = ctypes.c_void_p()
+    _check(None, load().asaga_create(ctypes.byref(ctx), ctypes.byref(problem.struct), ctypes.byref(options)))
+    return ctx.value
+
+
+def asaga_run(ctx: int, max_epochs: float, target_rel_subopt: float = 0.0, f_star: float = float("nan")):
+    """Returns (status, asaga_result); raises only on EINVAL / ENOMEM / ECUDA."""
+    r = asaga_result()
+    s = load().asaga_run(ctx, float(max_epochs), float(target_rel_subopt), float(f_star), ctypes.byref(r))
+    if s in (EINVAL, ENOMEM, ECUDA):
+        raise AsagaError(s, asaga_last_error(ctx))
+    return s, r
+
+
+def asaga_run_indices(ctx: int, idx, on_device: bool = False) -> None:
+    if not on_device:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+    count = idx.shape[0] if hasattr(idx, "shape") else len(idx)
+    _check(ctx, load().asaga_run_indices(ctx, _ptr(idx), int(count), int(on_device)))
+
+
+def asaga_objective(ctx: int) -> float:
+    f = ctypes.c_double()
+    _check(ctx, load().asaga_objective(ctx, ctypes.byref(f)))
+    return f.value
+
+
+def asaga_full_grad(ctx: int, want_grad: bool = True):
+    """Returns (grad float64[d] or None, |grad|^2)."""
+    info = asaga_get_info(ctx)
+    g = np.empty(info["d"], dtype=np.float64) if want_grad else None
+    n2 = ctypes.c_double()
+    _check(ctx, load().asaga_full_grad(ctx, _ptr(g), ctypes.byref(n2)))
+    return g, n2.value
+
+
+def asaga_recompute_abar(ctx: int) -> float:
+    drift = ctypes.c_double()
+    _check(ctx, load().asaga_recompute_abar(ctx, ctypes.byref(drift)))
+    return drift.value
+
+
+def asaga_get_state(ctx: int):
+    """Returns (x float32[d], abar float32[d], alpha float32[n])."""
+    info = asaga_get_info(ctx)
+    x = np.empty(info["d"], dtype=np.float32)
+    abar = np.empty(info["d"], dtype=np.float32)
+    alpha = np.empty(info["n"], dtype=np.float32)
+    _check(ctx, load().asaga_get_state(ctx, _ptr(x), _ptr(abar), _ptr(alpha)))
+    return x, abar, alpha
+
+
+def asaga_set_state(ctx: int, x=None, abar=None, alpha=None, updates_done: int = 0) -> None:
+    conv = lambda a: None if a is None else np.ascontiguousarray(a, dtype=np.float32)
+    x, abar, alpha = conv(x), conv(abar), conv(alpha)
+    _check(ctx, load().asaga_set_state(ctx, _ptr(x), _ptr(abar), _ptr(alpha), int(updates_done)))
+
+
+def asaga_get_info(ctx: int) -> dict:
+    i = asaga_info()
+    _check(ctx, load().asaga_get_info(ctx, ctypes.byref(i)))
+    return i.as_dict()
+
+
+def asaga_last_error(ctx: Optional[int]) -> str:
+    return load().asaga_last_error(ctx).decode()
+
+
+def asaga_status_string(s: int) -> str:
+    return load().asaga_status_string(int(s)).decode()
+
+
+def asaga_destroy(ctx: Optional[int]) -> None:
+    if ctx:
+        load().asaga_destroy(ctx)
+
+
+class Context:
+    """Owning wrapper: creates a context from a generated problem and frees it."""
+
+    def __init__(self, p, *, storage: Optional[str] = None, values_dtype: str = "f64", **options):
+        opts = dict(loss=p.loss, lam=p.lam, storage_dtype=storage or p.storage)
+        if opts["storage_dtype"] == "f64":
+            opts["storage_dtype"] = "f32"
+        opts.update(options)
+        self.problem = host_problem(p, values_dtype)
+        self.options = asaga_default_options(**opts)
+        self.ctx = asaga_create(self.problem, self.options)
+
+    def close(self):
+        if self.ctx:
+            asaga_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

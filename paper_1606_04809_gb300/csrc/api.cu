@@ -1,0 +1,709 @@
+// Host side of the C ABI declared in include/asaga.h: validation, device
+// layout, set-up (D, L, gamma), the segment loop of asaga_run and the float64
+// evaluations.  All device work of a context is ordered on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "asaga.h"
+#include "asaga_internal.h"
+
+using namespace asaga;
+
+struct asaga_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int sms = 1;
+
+    int64_t n = 0, d = 0, nnz = 0, max_row_len = 0;
+    bool dense = false;
+    int loss = 0;
+    int vtype = kF32;
+    double lambda = 0, gamma = 0, L = 0, delta = 0;
+    int stride = 1;
+    int warps = 1;
+    bool deterministic = false;
+    uint64_t seed = 0;
+    int epochs_per_segment = 1;
+    int abar_every = 0;
+    double timeout_s = 0;
+    int64_t updates_done = 0;
+    int eval_grid = 1;
+    int64_t launches = 0;
+    int64_t device_bytes = 0;
+
+    // device buffers
+    int64_t *row_ptr = nullptr;
+    int32_t *col_idx = nullptr;
+    void *values = nullptr;
+    float *lab32 = nullptr;
+    double *lab64 = nullptr;
+    float *alpha = nullptr;
+    float4 *state = nullptr;
+    double *acc64 = nullptr;
+    double *partial = nullptr;
+    double *dout = nullptr;  // [0] f, [1..] small results
+    int *status = nullptr;
+    int64_t *idx_buf = nullptr;
+    int64_t idx_cap = 0;
+    double *hout = nullptr;  // pinned mirror of dout
+    int *hstatus = nullptr;  // pinned
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+const char *kStatusNames[] = {"ASAGA_OK", "ASAGA_EINVAL", "ASAGA_ENOMEM", "ASAGA_ECUDA",
+                              "ASAGA_ETIMEOUT", "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED"};
+
+asaga_status fail(std::string *err, asaga_status s, const std::string &msg) {
+    if (err) *err = msg;
+    return s;
+}
+
+asaga_status cuda_fail(std::string *err, cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky-free error
+    if (err) *err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? ASAGA_ENOMEM : ASAGA_ECUDA;
+}
+
+#define CK(call, what)                                                   \
+    do {                                                                 \
+        cudaError_t e_ = (call);                                         \
+        if (e_ != cudaSuccess) return cuda_fail(err, e_, what);          \
+    } while (0)
+
+size_t dtype_size(int dt) {
+    switch (dt) {
+    case ASAGA_F64: return 8;
+    case ASAGA_F32: return 4;
+    case ASAGA_BF16:
+    case ASAGA_F16: return 2;
+    default: return 0;
+    }
+}
+
+bool value_finite(const void *vals, int dt, int64_t k) {
+    switch (dt) {
+    case ASAGA_F64: return std::isfinite(((const double *)vals)[k]);
+    case ASAGA_F32: return std::isfinite(((const float *)vals)[k]);
+    case ASAGA_BF16: return (((const uint16_t *)vals)[k] & 0x7F80u) != 0x7F80u;
+    case ASAGA_F16: return (((const uint16_t *)vals)[k] & 0x7C00u) != 0x7C00u;
+    default: return false;
+    }
+}
+
+template <typename T>
+asaga_status dev_alloc(T **p, size_t count, asaga_ctx *c, std::string *err, const char *what) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) return cuda_fail(err, e, what);
+    c->device_bytes += (int64_t)bytes;
+    return ASAGA_OK;
+}
+
+#define TRY(expr)                                 \
+    do {                                          \
+        asaga_status s_ = (expr);                 \
+        if (s_ != ASAGA_OK) return s_;            \
+    } while (0)
+
+// Host-side validation of the problem (copies device inputs to the host
+// first).  Fills max_row_len.
+asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *max_row_len, std::string *err) {
+    if (!p || !o) return fail(err, ASAGA_EINVAL, "problem or options is NULL");
+    if (p->n < 1 || p->d < 1) return fail(err, ASAGA_EINVAL, "n and d must be >= 1");
+    if (p->d > (int64_t)INT32_MAX) return fail(err, ASAGA_EINVAL, "d must fit in int32");
+    if (o->loss != ASAGA_LOSS_LOGISTIC && o->loss != ASAGA_LOSS_SQUARED)
+        return fail(err, ASAGA_EINVAL, "unknown loss");
+    if (!std::isfinite(o->lambda) || o->lambda < 0) return fail(err, ASAGA_EINVAL, "lambda must be finite and >= 0");
+    if (!std::isfinite(o->gamma)) return fail(err, ASAGA_EINVAL, "gamma must be finite");
+    if (o->storage_dtype != ASAGA_F32 && o->storage_dtype != ASAGA_BF16 && o->storage_dtype != ASAGA_F16)
+        return fail(err, ASAGA_EINVAL, "storage_dtype must be F32, BF16 or F16");
+    if (dtype_size(p->values_dtype) == 0) return fail(err, ASAGA_EINVAL, "unknown values_dtype");
+    if (o->epochs_per_segment < 0 || o->abar_recompute_every < 0 || o->max_warps < 0 ||
+        o->column_stride < 0 || !(o->timeout_s >= 0))
+        return fail(err, ASAGA_EINVAL, "negative option");
+    if (!p->values || !p->labels) return fail(err, ASAGA_EINVAL, "values or labels is NULL");
+    int64_t nnz = p->nnz;
+    if (p->dense) {
+        if (p->d > 0 && p->n > INT64_MAX / p->d) return fail(err, ASAGA_EINVAL, "n*d overflows");
+        if (nnz != 0 && nnz != p->n * p->d) return fail(err, ASAGA_EINVAL, "dense problem needs nnz = n*d (or 0)");
+        nnz = p->n * p->d;
+    } else {
+        if (nnz < 0) return fail(err, ASAGA_EINVAL, "nnz < 0");
+        if (!p->row_ptr || (!p->col_idx && nnz > 0)) return fail(err, ASAGA_EINVAL, "row_ptr or col_idx is NULL");
+    }
+    const size_t vsz = dtype_size(p->values_dtype);
+    std::vector<int64_t> rp_h;
+    std::vector<int32_t> ci_h;
+    std::vector<double> lab_h;
+    std::vector<unsigned char> val_h;
+    const int64_t *rp = p->row_ptr;
+    const int32_t *ci = p->col_idx;
+    const double *lab = p->labels;
+    const void *val = p->values;
+    if (p->on_device) {
+        cudaError_t e;
+        lab_h.resize(p->n);
+        val_h.resize((size_t)nnz * vsz);
+        if ((e = cudaMemcpy(lab_h.data(), p->labels, p->n * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(err, e, "copy labels for validation");
+        if (nnz > 0 &&
+            (e = cudaMemcpy(val_h.data(), p->values, (size_t)nnz * vsz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(err, e, "copy values for validation");
+        lab = lab_h.data();
+        val = val_h.data();
+        if (!p->dense) {
+            rp_h.resize(p->n + 1);
+            ci_h.resize(nnz);
+            if ((e = cudaMemcpy(rp_h.data(), p->row_ptr, (p->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost)) !=
+                cudaSuccess)
+                return cuda_fail(err, e, "copy row_ptr for validation");
+            if (nnz > 0 &&
+                (e = cudaMemcpy(ci_h.data(), p->col_idx, nnz * sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return cuda_fail(err, e, "copy col_idx for validation");
+            rp = rp_h.data();
+            ci = ci_h.data();
+        }
+    }
+    for (int64_t i = 0; i < p->n; ++i) {
+        if (!std::isfinite(lab[i])) return fail(err, ASAGA_EINVAL, "non-finite label at row " + std::to_string(i));
+        if (o->loss == ASAGA_LOSS_LOGISTIC && lab[i] != 1.0 && lab[i] != -1.0)
+            return fail(err, ASAGA_EINVAL, "logistic label not +-1 at row " + std::to_string(i));
+    }
+    for (int64_t k = 0; k < nnz; ++k)
+        if (!value_finite(val, p->values_dtype, k))
+            return fail(err, ASAGA_EINVAL, "non-finite value at entry " + std::to_string(k));
+    int64_t mrl = 0;
+    if (p->dense) {
+        mrl = p->d;
+    } else {
+        if (rp[0] != 0 || rp[p->n] != nnz) return fail(err, ASAGA_EINVAL, "row_ptr must start at 0 and end at nnz");
+        std::vector<int64_t> last(p->d, -1);
+        for (int64_t i = 0; i < p->n; ++i) {
+            if (rp[i + 1] < rp[i]) return fail(err, ASAGA_EINVAL, "row_ptr decreases at row " + std::to_string(i));
+            const int64_t len = rp[i + 1] - rp[i];
+            if (len > INT32_MAX) return fail(err, ASAGA_EINVAL, "row too long");
+            if (len > mrl) mrl = len;
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t c = ci[k];
+                if (c < 0 || c >= p->d)
+                    return fail(err, ASAGA_EINVAL, "column index out of range at entry " + std::to_string(k));
+                if (last[c] == i)
+                    return fail(err, ASAGA_EINVAL, "repeated column in row " + std::to_string(i));
+                last[c] = i;
+            }
+        }
+    }
+    *max_row_len = mrl;
+    return ASAGA_OK;
+}
+
+EvalParams eval_params(const asaga_ctx *c) {
+    EvalParams e;
+    e.n = c->n;
+    e.d = c->d;
+    e.row_ptr = c->row_ptr;
+    e.col_idx = c->col_idx;
+    e.values = c->values;
+    e.labels = c->lab64;
+    e.alpha = c->alpha;
+    e.state = c->state;
+    e.stride = c->stride;
+    e.loss = c->loss;
+    e.lambda = c->lambda;
+    return e;
+}
+
+// Launches the float64 objective; result lands in c->dout[0].
+asaga_status enqueue_objective(asaga_ctx *c, std::string *err) {
+    const EvalParams e = eval_params(c);
+    CK(launch_objective_rows(e, c->vtype, c->dense, c->eval_grid, c->partial, c->stream), "objective kernel");
+    CK(launch_objective_finish(c->partial, c->eval_grid, 1.0 / (double)c->n, c->lambda, c->dout, c->stream),
+       "objective finish");
+    c->launches += 2;
+    return ASAGA_OK;
+}
+
+// Recomputes abar from alpha in float64; max drift lands in c->dout[1].
+asaga_status enqueue_recompute(asaga_ctx *c, std::string *err) {
+    const EvalParams e = eval_params(c);
+    CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
+    CK(launch_scatter_rows(e, c->vtype, c->dense, 1, c->eval_grid, c->acc64, c->stream), "abar scatter");
+    CK(launch_column_finish(e, 1, c->eval_grid, c->acc64, c->partial, c->stream), "abar finish");
+    CK(launch_reduce_partials(c->partial, c->eval_grid, 1, c->dout + 1, c->stream), "abar reduce");
+    c->launches += 3;
+    return ASAGA_OK;
+}
+
+asaga_status stream_sync(asaga_ctx *c, std::string *err) {
+    CK(cudaStreamSynchronize(c->stream), "stream synchronize");
+    return ASAGA_OK;
+}
+
+asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
+    int64_t mrl = 0;
+    TRY(validate(p, o, &mrl, err));
+    CK(cudaGetDevice(&c->device), "cudaGetDevice");
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
+    c->sms = prop.multiProcessorCount;
+    if (o->cuda_stream) {
+        c->stream = (cudaStream_t)o->cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        c->own_stream = true;
+    }
+    for (auto &ev : c->ev) CK(cudaEventCreate(&ev), "cudaEventCreate");
+
+    c->n = p->n;
+    c->d = p->d;
+    c->dense = p->dense != 0;
+    c->nnz = c->dense ? p->n * p->d : p->nnz;
+    c->max_row_len = mrl;
+    c->loss = o->loss;
+    c->vtype = o->storage_dtype == ASAGA_F32 ? kF32 : (o->storage_dtype == ASAGA_BF16 ? kBF16 : kF16);
+    c->lambda = o->lambda;
+    c->deterministic = o->deterministic != 0;
+    c->seed = o->seed;
+    c->epochs_per_segment = o->epochs_per_segment > 0 ? o->epochs_per_segment : 1;
+    c->abar_every = o->abar_recompute_every;
+    c->timeout_s = o->timeout_s;
+    c->stride = o->column_stride > 0 ? o->column_stride : (c->d <= 1024 ? 8 : 1);
+
+    const size_t vsz_in = dtype_size(p->values_dtype);
+    const size_t vsz = c->vtype == kF32 ? 4 : 2;
+    const cudaMemcpyKind kind = p->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+    // problem
+    if (!c->dense) {
+        TRY(dev_alloc(&c->row_ptr, c->n + 1, c, err, "alloc row_ptr"));
+        TRY(dev_alloc(&c->col_idx, c->nnz, c, err, "alloc col_idx"));
+        CK(cudaMemcpyAsync(c->row_ptr, p->row_ptr, (c->n + 1) * sizeof(int64_t), kind, c->stream), "copy row_ptr");
+        if (c->nnz > 0)
+            CK(cudaMemcpyAsync(c->col_idx, p->col_idx, c->nnz * sizeof(int32_t), kind, c->stream), "copy col_idx");
+    }
+    unsigned char *vals = nullptr;
+    TRY(dev_alloc(&vals, (size_t)c->nnz * vsz, c, err, "alloc values"));
+    c->values = vals;
+    const int in_dt = (int)p->values_dtype;
+    const int want_dt = (int)o->storage_dtype;
+    if (c->nnz > 0) {
+        if (in_dt == want_dt) {
+            CK(cudaMemcpyAsync(c->values, p->values, (size_t)c->nnz * vsz, kind, c->stream), "copy values");
+        } else {
+            const void *src = p->values;
+            void *staging = nullptr;
+            if (!p->on_device) {
+                CK(cudaMallocAsync(&staging, (size_t)c->nnz * vsz_in, c->stream), "alloc staging");
+                CK(cudaMemcpyAsync(staging, p->values, (size_t)c->nnz * vsz_in, cudaMemcpyHostToDevice, c->stream),
+                   "copy values");
+                src = staging;
+            }
+            cudaError_t e = launch_convert(src, in_dt, c->values, c->vtype, c->nnz, c->stream);
+            ++c->launches;
+            if (staging) cudaFreeAsync(staging, c->stream);
+            if (e != cudaSuccess) return cuda_fail(err, e, "convert values");
+        }
+    }
+    TRY(dev_alloc(&c->lab64, c->n, c, err, "alloc labels"));
+    TRY(dev_alloc(&c->lab32, c->n, c, err, "alloc labels"));
+    CK(cudaMemcpyAsync(c->lab64, p->labels, c->n * sizeof(double), kind, c->stream), "copy labels");
+    CK(launch_labels(c->lab64, c->lab32, c->n, c->stream), "labels kernel");
+
+    // state
+    TRY(dev_alloc(&c->alpha, c->n, c, err, "alloc alpha"));
+    CK(cudaMemsetAsync(c->alpha, 0, c->n * sizeof(float), c->stream), "memset alpha");
+    TRY(dev_alloc(&c->state, (size_t)c->d * c->stride, c, err, "alloc state"));
+    CK(cudaMemsetAsync(c->state, 0, (size_t)c->d * c->stride * sizeof(float4), c->stream), "memset state");
+    TRY(dev_alloc(&c->acc64, c->d, c, err, "alloc scratch"));
+    c->eval_grid = c->sms * 4;
+    if (c->eval_grid > kMaxPartials) c->eval_grid = kMaxPartials;
+    TRY(dev_alloc(&c->partial, 2 * (size_t)kMaxPartials, c, err, "alloc partials"));
+    TRY(dev_alloc(&c->dout, 8, c, err, "alloc out"));
+    TRY(dev_alloc(&c->status, 4, c, err, "alloc status"));
+    CK(cudaMallocHost((void **)&c->hout, 8 * sizeof(double)), "alloc pinned");
+    CK(cudaMallocHost((void **)&c->hstatus, 4 * sizeof(int)), "alloc pinned");
+
+    // D from the column counts (Sec. 2); dense rows give D = 1
+    int *count = nullptr;
+    std::vector<int> count_h;
+    if (!c->dense) {
+        CK(cudaMallocAsync((void **)&count, c->d * sizeof(int), c->stream), "alloc counts");
+        CK(cudaMemsetAsync(count, 0, c->d * sizeof(int), c->stream), "memset counts");
+        CK(launch_count_columns(c->col_idx, c->nnz, count, c->stream), "count kernel");
+        ++c->launches;
+    }
+    CK(launch_init_state(c->state, c->stride, c->d, count, c->n, c->stream), "init state");
+    ++c->launches;
+    if (count) {
+        count_h.resize(c->d);
+        CK(cudaMemcpyAsync(count_h.data(), count, c->d * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "copy counts");
+        CK(cudaFreeAsync(count, c->stream), "free counts");
+    }
+    // L = c max_i |a_i|^2 + lambda on the stored values
+    const EvalParams e = eval_params(c);
+    CK(launch_max_row_norm2(e, c->vtype, c->dense, c->eval_grid, c->partial, c->dout, c->stream), "norm kernel");
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy norm");
+    TRY(stream_sync(c, err));
+    const double cl = c->loss == ASAGA_LOSS_LOGISTIC ? 0.25 : 1.0;
+    c->L = cl * c->hout[0] + c->lambda;
+    c->gamma = o->gamma > 0 ? o->gamma : (c->L > 0 ? 1.0 / (3.0 * c->L) : 1.0);
+    if (c->dense) {
+        c->delta = 1.0;
+    } else {
+        int mx = 0;
+        for (int v : count_h) mx = v > mx ? v : mx;
+        c->delta = (double)mx / (double)c->n;
+    }
+
+    // concurrency: resident warps of the update kernel, bounded by n so that
+    // the overlap stays far below n/10 (Theorem 2's condition)
+    const int bps = update_max_blocks_per_sm(c->vtype, c->dense);
+    const int64_t resident = (int64_t)c->sms * bps * (kUpdateBlock / 32);
+    int64_t w = o->max_warps > 0 ? o->max_warps : std::max<int64_t>(1, c->n / 64);
+    if (w > resident) w = resident;
+    if (c->deterministic) w = 1;
+    c->warps = (int)w;
+    return ASAGA_OK;
+}
+
+void release(asaga_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->row_ptr);
+    cudaFree(c->col_idx);
+    cudaFree(c->values);
+    cudaFree(c->lab32);
+    cudaFree(c->lab64);
+    cudaFree(c->alpha);
+    cudaFree(c->state);
+    cudaFree(c->acc64);
+    cudaFree(c->partial);
+    cudaFree(c->dout);
+    cudaFree(c->status);
+    cudaFree(c->idx_buf);
+    if (c->hout) cudaFreeHost(c->hout);
+    if (c->hstatus) cudaFreeHost(c->hstatus);
+    for (auto &ev : c->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+UpdateParams update_params(const asaga_ctx *c) {
+    UpdateParams u;
+    u.n = c->n;
+    u.d = c->d;
+    u.row_ptr = c->row_ptr;
+    u.col_idx = c->col_idx;
+    u.values = c->values;
+    u.labels = c->lab32;
+    u.alpha = c->alpha;
+    u.state = c->state;
+    u.stride = c->stride;
+    u.loss = c->loss;
+    u.gamma = (float)c->gamma;
+    u.lambda = (float)c->lambda;
+    u.inv_n = (float)(1.0 / (double)c->n);
+    u.seed = c->seed;
+    u.t_begin = 0;
+    u.count = 0;
+    u.nwarps = c->warps;
+    u.idx = nullptr;
+    u.fence_each = c->warps == 1 ? 1 : 0;
+    u.deadline_ns = 0;
+    u.status = c->status;
+    return u;
+}
+
+asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
+    const int block = u.nwarps == 1 ? 32 : kUpdateBlock;
+    const int wpb = block / 32;
+    const int grid = (u.nwarps + wpb - 1) / wpb;
+    CK(launch_update(u, c->vtype, c->dense, grid, block, c->stream), "update kernel");
+    ++c->launches;
+    return ASAGA_OK;
+}
+
+asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_star, asaga_result *res,
+                      std::string *err) {
+    if (!(max_epochs >= 0) || !std::isfinite(max_epochs)) return fail(err, ASAGA_EINVAL, "max_epochs must be >= 0");
+    if (!std::isfinite(target)) return fail(err, ASAGA_EINVAL, "target must be finite");
+    if (target > 0 && (!std::isfinite(f_star) || f_star == 0.0))
+        return fail(err, ASAGA_EINVAL, "f_star must be finite and nonzero when a target is set");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const auto t0 = std::chrono::steady_clock::now();
+    asaga_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.f_last = NAN;
+    r.rel_subopt = NAN;
+    const int64_t launches0 = c->launches;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "memset status");
+    double epochs_done = 0;
+    asaga_status st = target > 0 ? ASAGA_ENOTCONVERGED : ASAGA_OK;
+    int64_t seg = 0;
+    while (epochs_done < max_epochs) {
+        const double ep = std::min((double)c->epochs_per_segment, max_epochs - epochs_done);
+        const int64_t count = (int64_t)std::llround(ep * (double)c->n);
+        UpdateParams u = update_params(c);
+        u.t_begin = (uint64_t)c->updates_done;
+        u.count = count;
+        if (c->timeout_s > 0) {
+            const double left = c->timeout_s -
+                                std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            u.deadline_ns = left > 0 ? (uint64_t)(left * 1e9) : 1;
+        }
+        CK(cudaEventRecord(c->ev[0], c->stream), "event");
+        if (count > 0) TRY(launch_updates(c, u, err));
+        CK(cudaEventRecord(c->ev[1], c->stream), "event");
+        ++seg;
+        if (c->abar_every > 0 && seg % c->abar_every == 0) TRY(enqueue_recompute(c, err));
+        TRY(enqueue_objective(c, err));
+        CK(cudaEventRecord(c->ev[2], c->stream), "event");
+        CK(cudaMemcpyAsync(c->hout, c->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
+        CK(cudaMemcpyAsync(c->hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
+        TRY(stream_sync(c, err));
+        float ms_solve = 0, ms_eval = 0;
+        cudaEventElapsedTime(&ms_solve, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&ms_eval, c->ev[1], c->ev[2]);
+        r.solver_seconds += ms_solve * 1e-3;
+        r.eval_seconds += ms_eval * 1e-3;
+        c->updates_done += count;
+        r.updates += count;
+        epochs_done += ep;
+        r.segments = seg;
+        r.f_last = c->hout[0];
+        if (c->abar_every > 0 && seg % c->abar_every == 0) r.abar_drift = c->hout[1];
+        if (target > 0 || std::isfinite(f_star)) r.rel_subopt = (r.f_last - f_star) / std::fabs(f_star);
+        if (*c->hstatus & 1) {
+            st = ASAGA_ETIMEOUT;
+            fail(err, st, "timeout");
+            break;
+        }
+        if (!std::isfinite(r.f_last)) {
+            st = ASAGA_EDIVERGED;
+            fail(err, st, "objective is not finite");
+            break;
+        }
+        if (target > 0 && r.rel_subopt <= target) {
+            st = ASAGA_OK;
+            break;
+        }
+    }
+    if (seg == 0) {  // max_epochs == 0: report f at the current iterate
+        TRY(enqueue_objective(c, err));
+        CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
+        TRY(stream_sync(c, err));
+        r.f_last = c->hout[0];
+        if (std::isfinite(f_star) && f_star != 0) r.rel_subopt = (r.f_last - f_star) / std::fabs(f_star);
+        if (target > 0 && r.rel_subopt <= target) st = ASAGA_OK;
+    }
+    r.epochs = epochs_done;
+    r.kernel_launches = c->launches - launches0;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (res) *res = r;
+    if (st == ASAGA_ENOTCONVERGED) fail(err, st, "max_epochs reached before the target");
+    return st;
+}
+
+asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, int on_device, std::string *err) {
+    if (count < 0) return fail(err, ASAGA_EINVAL, "count < 0");
+    if (count == 0) return ASAGA_OK;
+    if (!idx) return fail(err, ASAGA_EINVAL, "idx is NULL");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int64_t *didx = idx;
+    if (!on_device) {
+        for (int64_t t = 0; t < count; ++t)
+            if (idx[t] < 0 || idx[t] >= c->n) return fail(err, ASAGA_EINVAL, "index out of range at " + std::to_string(t));
+        if (count > c->idx_cap) {
+            CK(cudaStreamSynchronize(c->stream), "sync");
+            if (c->idx_buf) {
+                cudaFree(c->idx_buf);
+                c->device_bytes -= c->idx_cap * (int64_t)sizeof(int64_t);
+                c->idx_buf = nullptr;
+                c->idx_cap = 0;
+            }
+            TRY(dev_alloc(&c->idx_buf, count, c, err, "alloc index buffer"));
+            c->idx_cap = count;
+        }
+        CK(cudaMemcpyAsync(c->idx_buf, idx, count * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream), "copy idx");
+        didx = c->idx_buf;
+    }
+    UpdateParams u = update_params(c);
+    u.nwarps = 1;
+    u.fence_each = 1;
+    u.idx = didx;
+    u.count = count;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "memset status");
+    TRY(launch_updates(c, u, err));
+    CK(cudaMemcpyAsync(c->hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
+    TRY(stream_sync(c, err));
+    if (*c->hstatus & 2) return fail(err, ASAGA_EINVAL, "index out of range in device index array");
+    return ASAGA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void asaga_default_options(asaga_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->loss = ASAGA_LOSS_LOGISTIC;
+    o->lambda = 0.0;
+    o->gamma = 0.0;
+    o->storage_dtype = ASAGA_F32;
+    o->max_warps = 0;
+    o->deterministic = 0;
+    o->seed = 0;
+    o->epochs_per_segment = 1;
+    o->abar_recompute_every = 0;
+    o->timeout_s = 0.0;
+    o->cuda_stream = nullptr;
+    o->column_stride = 0;
+}
+
+asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {
+    if (!out) {
+        g_create_err = "out is NULL";
+        return ASAGA_EINVAL;
+    }
+    *out = nullptr;
+    asaga_ctx *c = new (std::nothrow) asaga_ctx();
+    if (!c) {
+        g_create_err = "host allocation failed";
+        return ASAGA_ENOMEM;
+    }
+    std::string err;
+    asaga_status s = create_impl(c, p, o, &err);
+    if (s != ASAGA_OK) {
+        g_create_err = err;
+        release(c);
+        return s;
+    }
+    *out = c;
+    return ASAGA_OK;
+}
+
+asaga_status asaga_run(asaga_ctx *c, double max_epochs, double target, double f_star, asaga_result *res) {
+    if (!c) return ASAGA_EINVAL;
+    return run_impl(c, max_epochs, target, f_star, res, &c->err);
+}
+
+asaga_status asaga_run_indices(asaga_ctx *c, const int64_t *idx, int64_t count, int idx_on_device) {
+    if (!c) return ASAGA_EINVAL;
+    return run_indices_impl(c, idx, count, idx_on_device, &c->err);
+}
+
+asaga_status asaga_objective(asaga_ctx *c, double *f) {
+    if (!c || !f) return ASAGA_EINVAL;
+    std::string *err = &c->err;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    TRY(enqueue_objective(c, err));
+    CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
+    TRY(stream_sync(c, err));
+    *f = c->hout[0];
+    return ASAGA_OK;
+}
+
+asaga_status asaga_full_grad(asaga_ctx *c, double *grad, double *norm2) {
+    if (!c) return ASAGA_EINVAL;
+    std::string *err = &c->err;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const EvalParams e = eval_params(c);
+    CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
+    CK(launch_scatter_rows(e, c->vtype, c->dense, 0, c->eval_grid, c->acc64, c->stream), "gradient scatter");
+    CK(launch_column_finish(e, 0, c->eval_grid, c->acc64, c->partial, c->stream), "gradient finish");
+    CK(launch_reduce_partials(c->partial, c->eval_grid, 0, c->dout + 2, c->stream), "gradient reduce");
+    c->launches += 3;
+    CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy norm");
+    if (grad) CK(cudaMemcpyAsync(grad, c->acc64, c->d * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy grad");
+    TRY(stream_sync(c, err));
+    if (norm2) *norm2 = c->hout[2];
+    return ASAGA_OK;
+}
+
+asaga_status asaga_recompute_abar(asaga_ctx *c, double *drift) {
+    if (!c) return ASAGA_EINVAL;
+    std::string *err = &c->err;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    TRY(enqueue_recompute(c, err));
+    CK(cudaMemcpyAsync(c->hout + 1, c->dout + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy drift");
+    TRY(stream_sync(c, err));
+    if (drift) *drift = c->hout[1];
+    return ASAGA_OK;
+}
+
+asaga_status asaga_get_state(asaga_ctx *c, float *x, float *abar, float *alpha) {
+    if (!c) return ASAGA_EINVAL;
+    std::string *err = &c->err;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t pitch = (size_t)c->stride * sizeof(float4);
+    if (x) CK(cudaMemcpy2DAsync(x, sizeof(float), (const char *)c->state, pitch, sizeof(float), c->d,
+                                cudaMemcpyDeviceToHost, c->stream), "copy x");
+    if (abar) CK(cudaMemcpy2DAsync(abar, sizeof(float), (const char *)c->state + sizeof(float), pitch, sizeof(float),
+                                   c->d, cudaMemcpyDeviceToHost, c->stream), "copy abar");
+    if (alpha) CK(cudaMemcpyAsync(alpha, c->alpha, c->n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy alpha");
+    TRY(stream_sync(c, err));
+    return ASAGA_OK;
+}
+
+asaga_status asaga_set_state(asaga_ctx *c, const float *x, const float *abar, const float *alpha,
+                             int64_t updates_done) {
+    if (!c) return ASAGA_EINVAL;
+    if (updates_done < 0) return fail(&c->err, ASAGA_EINVAL, "updates_done < 0");
+    std::string *err = &c->err;
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const size_t pitch = (size_t)c->stride * sizeof(float4);
+    if (x) CK(cudaMemcpy2DAsync((char *)c->state, pitch, x, sizeof(float), sizeof(float), c->d,
+                                cudaMemcpyHostToDevice, c->stream), "copy x");
+    if (abar) CK(cudaMemcpy2DAsync((char *)c->state + sizeof(float), pitch, abar, sizeof(float), sizeof(float), c->d,
+                                   cudaMemcpyHostToDevice, c->stream), "copy abar");
+    if (alpha) CK(cudaMemcpyAsync(c->alpha, alpha, c->n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy alpha");
+    TRY(stream_sync(c, err));
+    c->updates_done = updates_done;
+    return ASAGA_OK;
+}
+
+asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
+    if (!c || !info) return ASAGA_EINVAL;
+    info->n = c->n;
+    info->d = c->d;
+    info->nnz = c->nnz;
+    info->L = c->L;
+    info->gamma = c->gamma;
+    info->delta = c->delta;
+    info->warps = c->warps;
+    info->column_stride = c->stride;
+    info->device_bytes = c->device_bytes;
+    info->max_row_len = c->max_row_len;
+    return ASAGA_OK;
+}
+
+const char *asaga_last_error(const asaga_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+const char *asaga_status_string(asaga_status s) {
+    if ((int)s < 0 || (int)s > 6) return "ASAGA_UNKNOWN";
+    return kStatusNames[(int)s];
+}
+
+void asaga_destroy(asaga_ctx *c) { release(c); }
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// Internal declarations shared by the solver's CUDA translation units:
+// launch parameters of every kernel and the host-side launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace asaga {
+
+// Device element type of A's values.
+enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3 };
+
+// Per-column solver state, 16 bytes: the iterate x_v, the running average
+// abar_v and the reweighting D_v, gathered by one 16-byte load and updated
+// (x_v, abar_v) by one vector atomic.  Columns are spaced `stride` float4s
+// apart.
+//   .x = x_v, .y = abar_v, .z = D_v, .w = unused (0)
+
+// Launch parameters of the asynchronous update kernel (one update = one
+// sampled row, Algorithm 2).
+struct UpdateParams {
+    int64_t n, d;
+    const int64_t *row_ptr;   // n+1 (sparse) or nullptr (dense)
+    const int32_t *col_idx;   // nnz (sparse) or nullptr (dense)
+    const void *values;       // nnz (or n*d) of the storage type
+    const float *labels;      // n, float32 copy for the update
+    float *alpha;             // n, scalar memory per sample
+    float4 *state;            // d * stride
+    int stride;               // float4s between consecutive columns
+    int loss;                 // 0 logistic, 1 squared
+    float gamma, lambda, inv_n;
+    uint64_t seed;            // sampler seed
+    uint64_t t_begin;         // global index of this launch's first update
+    int64_t count;            // updates in this launch
+    int nwarps;               // warps taking part (static strided split)
+    const int64_t *idx;       // explicit row sequence (deterministic replay) or nullptr
+    int fence_each;           // 1: fence after every update (single-warp order)
+    uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
+    int *status;              // bit 0: timed out, bit 1: bad index
+};
+
+// Float64 evaluation parameters (objective, gradient, abar recomputation).
+struct EvalParams {
+    int64_t n, d;
+    const int64_t *row_ptr;
+    const int32_t *col_idx;
+    const void *values;
+    const double *labels;     // n, float64
+    const float *alpha;       // n
+    float4 *state;
+    int stride;
+    int loss;
+    double lambda;
+};
+
+constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
+constexpr int kEvalBlock = 256;
+constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
+
+// update.cu
+cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
+                          cudaStream_t s);
+int update_max_blocks_per_sm(int vtype, bool dense);
+
+// eval.cu
+// partial[0..grid) <- per-block sums of phi_i(a_i.x); partial[grid..2grid) <- sums of x_v^2.
+cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, int grid,
+                                  double *partial, cudaStream_t s);
+// out[0] <- (sum partial[0..grid))/n + lambda/2 (sum partial[grid..2grid)).
+cudaError_t launch_objective_finish(const double *partial, int grid, double inv_n, double lambda,
+                                    double *out, cudaStream_t s);
+// acc[v] += sum_i w_i a_iv with w_i = phi'_i(a_i.x)/n (mode 0) or alpha_i/n (mode 1).
+cudaError_t launch_scatter_rows(const EvalParams &p, int vtype, bool dense, int mode, int grid,
+                                double *acc, cudaStream_t s);
+// mode 0 (gradient): acc[v] += lambda x_v; partial[b] <- block sums of acc[v]^2.
+// mode 1 (abar):     partial[b] <- block max |abar_v - acc[v]|, then abar_v <- (float)acc[v].
+cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double *acc,
+                                 double *partial, cudaStream_t s);
+// out[0] <- sum (mode 0) or max (mode 1) of partial[0..grid).
+cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out,
+                                   cudaStream_t s);
+
+// prep (eval.cu)
+cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s);
+// state[v] <- {0, 0, D_v, 0}, D_v = n/count_v (0 if count_v = 0); count may be nullptr (dense: D = 1).
+cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n,
+                              cudaStream_t s);
+// out[0] <- max_i sum_k a_ik^2 (float64) over the stored values.
+cudaError_t launch_max_row_norm2(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
+                                 double *out, cudaStream_t s);
+// dst (vtype) <- src (src_dtype: 0 f64, 1 f32, 2 bf16, 3 f16), count elements.
+cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype, int64_t count,
+                           cudaStream_t s);
+cudaError_t launch_labels(const double *lab64, float *lab32, int64_t n, cudaStream_t s);
+
+}  // namespace asaga

@@ -1,0 +1,103 @@
+// Device helpers shared by the solver's kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace asaga {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+// Streaming read of A (each row is read once per visit; evict-first so that
+// the solver state keeps the L2).
+template <typename T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+// Read of shared state at L2 (bypasses L1, which is not coherent with the
+// atomics other SMs apply).
+__device__ __forceinline__ float4 ld_state(const float4 *p) { return __ldcg(p); }
+
+// x_v += dx and abar_v += dab as one vector reduction at L2 (each element
+// is added atomically; nothing is returned).
+__device__ __forceinline__ void red_add_v2(float4 *p, float dx, float dab) {
+    asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(dx), "f"(dab)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
+// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used as a counter-based
+// generator: output number t of the stream with the given seed.
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
+    uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Row index of update t: uniform in [0, n) with replacement (Algorithm 2
+// samples i before reading anything), by multiply-high range reduction.
+__device__ __forceinline__ int64_t sample_row(uint64_t seed, uint64_t t, int64_t n) {
+    return (int64_t)__umul64hi(splitmix64_at(seed, t), (uint64_t)n);
+}
+
+// phi'(z) in float32.  Logistic: -b / (1 + exp(b z)); squared: z - y.
+__device__ __forceinline__ float phi_prime_f32(int loss, float z, float b) {
+    if (loss == 0) {
+        float t = b * z;
+        float e = expf(-fabsf(t));                       // in (0, 1]
+        float s = (t >= 0.f) ? e / (1.f + e) : 1.f / (1.f + e);  // 1 / (1 + exp(t))
+        return -b * s;
+    }
+    return z - b;
+}
+
+// phi(z) and phi'(z) in float64.
+__device__ __forceinline__ double phi_f64(int loss, double z, double b) {
+    if (loss == 0) {
+        double t = b * z;  // log(1 + exp(-t))
+        return fmax(-t, 0.0) + log1p(exp(-fabs(t)));
+    }
+    double r = z - b;
+    return 0.5 * r * r;
+}
+
+__device__ __forceinline__ double phi_prime_f64(int loss, double z, double b) {
+    if (loss == 0) {
+        double t = b * z;
+        double e = exp(-fabs(t));
+        double s = (t >= 0.0) ? e / (1.0 + e) : 1.0 / (1.0 + e);
+        return -b * s;
+    }
+    return z - b;
+}
+
+}  // namespace asaga

@@ -1,0 +1,352 @@
+// Float64 evaluation and set-up kernels of the ASAGA solver.
+//
+//   objective      f(x) = 1/n sum_i phi_i(a_i.x) + lambda/2 |x|^2  (Eq. finiteSum, Sec. 4.1)
+//   gradient       1/n A^T phi'(A x) + lambda x
+//   abar recompute abar = 1/n sum_i alpha_i a_i  (Sec. 2, definition of abar)
+//   set-up         column counts -> D_v = n / |{i : v in S_i}| (Sec. 2),
+//                  max_i |a_i|^2 for L, value conversion to the storage type.
+//
+// All sums run in float64 on float32 state and stored values widened
+// exactly.  Row sums use one warp per row (grid-stride); block results go to
+// a partial array reduced by a single block in a fixed order, so objective
+// values are bitwise reproducible.  Column scatters (A^T w) use float64
+// atomics at L2; on dense problems with few columns each block first
+// accumulates in shared memory.
+#include "asaga_internal.h"
+#include "device_common.cuh"
+
+namespace asaga {
+
+constexpr int kSmemCols = 2048;  // dense problems up to this d accumulate per block in shared memory
+
+template <typename T>
+__device__ __forceinline__ double row_dot(const EvalParams &P, const T *vals, int64_t start, int len,
+                                          bool dense, int lane) {
+    double z = 0.0;
+    for (int k = lane; k < len; k += 32) {
+        const int c = dense ? k : __ldg(P.col_idx + start + k);
+        z += (double)to_f32(vals[start + k]) * (double)ld_state(P.state + (int64_t)c * P.stride).x;
+    }
+    return warp_sum(z);
+}
+
+template <typename T, bool kDense>
+__device__ __forceinline__ void row_range(const EvalParams &P, int64_t i, int64_t &start, int &len) {
+    if (kDense) {
+        start = i * P.d;
+        len = (int)P.d;
+    } else {
+        start = P.row_ptr[i];
+        len = (int)(P.row_ptr[i + 1] - start);
+    }
+}
+
+// Deterministic block reduction (sum or max) of one double per thread.
+__device__ __forceinline__ double block_reduce(double v, bool is_max) {
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    v = is_max ? warp_max(v) : warp_sum(v);
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    double r = 0.0;
+    if (w == 0) {
+        r = lane < nw ? red[lane] : 0.0;
+        r = is_max ? warp_max(r) : warp_sum(r);
+    }
+    __syncthreads();
+    return r;  // valid in thread 0
+}
+
+template <typename T, bool kDense>
+__global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalParams P, double *partial) {
+    const T *vals = static_cast<const T *>(P.values);
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int64_t tw = (int64_t)gridDim.x * wpb;
+    double acc = 0.0;
+    for (int64_t i = gw; i < P.n; i += tw) {
+        int64_t start;
+        int len;
+        row_range<T, kDense>(P, i, start, len);
+        const double z = row_dot<T>(P, vals, start, len, kDense, lane);
+        if (lane == 0) acc += phi_f64(P.loss, z, P.labels[i]);
+    }
+    double xx = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.d; v += (int64_t)gridDim.x * blockDim.x) {
+        const double xv = ld_state(P.state + v * P.stride).x;
+        xx += xv * xv;
+    }
+    const double s1 = block_reduce(acc, false);
+    const double s2 = block_reduce(xx, false);
+    if (threadIdx.x == 0) {
+        partial[blockIdx.x] = s1;
+        partial[gridDim.x + blockIdx.x] = s2;
+    }
+}
+
+__global__ void objective_finish_kernel(const double *partial, int grid, double inv_n, double lambda,
+                                        double *out) {
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < grid; j += blockDim.x) {
+        a += partial[j];
+        b += partial[grid + j];
+    }
+    const double sa = block_reduce(a, false);
+    const double sb = block_reduce(b, false);
+    if (threadIdx.x == 0) out[0] = sa * inv_n + 0.5 * lambda * sb;
+}
+
+// acc[v] += sum_i w_i a_iv, w_i = phi'_i(a_i.x)/n (mode 0) or alpha_i/n (mode 1).
+template <typename T, bool kDense, bool kSmem>
+__global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalParams P, int mode, double *acc) {
+    extern __shared__ double sacc[];
+    const T *vals = static_cast<const T *>(P.values);
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int64_t tw = (int64_t)gridDim.x * wpb;
+    const double inv_n = 1.0 / (double)P.n;
+    if (kSmem) {
+        for (int v = threadIdx.x; v < P.d; v += blockDim.x) sacc[v] = 0.0;
+        __syncthreads();
+    }
+    for (int64_t i = gw; i < P.n; i += tw) {
+        int64_t start;
+        int len;
+        row_range<T, kDense>(P, i, start, len);
+        double w;
+        if (mode == 0) {
+            const double z = row_dot<T>(P, vals, start, len, kDense, lane);
+            w = phi_prime_f64(P.loss, z, P.labels[i]) * inv_n;
+        } else {
+            w = (double)P.alpha[i] * inv_n;
+        }
+        for (int k = lane; k < len; k += 32) {
+            const int c = kDense ? k : __ldg(P.col_idx + start + k);
+            const double contrib = w * (double)to_f32(vals[start + k]);
+            if (kSmem)
+                atomicAdd(sacc + c, contrib);
+            else
+                atomicAdd(acc + c, contrib);
+        }
+    }
+    if (kSmem) {
+        __syncthreads();
+        for (int v = threadIdx.x; v < P.d; v += blockDim.x) atomicAdd(acc + v, sacc[v]);
+    }
+}
+
+__global__ void __launch_bounds__(kEvalBlock) column_finish_kernel(const EvalParams P, int mode, double *acc,
+                                                                   double *partial) {
+    double local = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.d; v += (int64_t)gridDim.x * blockDim.x) {
+        float4 *sp = P.state + v * P.stride;
+        if (mode == 0) {
+            const double g = acc[v] + P.lambda * (double)sp->x;
+            acc[v] = g;
+            local += g * g;
+        } else {
+            const double exact = acc[v];
+            local = fmax(local, fabs((double)sp->y - exact));
+            sp->y = (float)exact;
+        }
+    }
+    const double r = block_reduce(local, mode == 1);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+__global__ void reduce_partials_kernel(const double *partial, int grid, int mode, double *out) {
+    double v = 0.0;
+    for (int j = threadIdx.x; j < grid; j += blockDim.x) v = mode == 1 ? fmax(v, partial[j]) : v + partial[j];
+    const double r = block_reduce(v, mode == 1);
+    if (threadIdx.x == 0) out[0] = r;
+}
+
+// ------------------------------------------------------------------ set-up
+
+__global__ void count_columns_kernel(const int32_t *col, int64_t nnz, int *count) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(count + col[k], 1);
+}
+
+__global__ void init_state_kernel(float4 *state, int stride, int64_t d, const int *count, int64_t n) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < d; v += (int64_t)gridDim.x * blockDim.x) {
+        float D = 1.f;
+        if (count) D = count[v] > 0 ? (float)((double)n / (double)count[v]) : 0.f;
+        state[v * stride] = make_float4(0.f, 0.f, D, 0.f);
+    }
+}
+
+template <typename T, bool kDense>
+__global__ void __launch_bounds__(kEvalBlock) row_norm2_kernel(const EvalParams P, double *partial) {
+    const T *vals = static_cast<const T *>(P.values);
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
+    const int64_t tw = (int64_t)gridDim.x * wpb;
+    double best = 0.0;
+    for (int64_t i = gw; i < P.n; i += tw) {
+        int64_t start;
+        int len;
+        row_range<T, kDense>(P, i, start, len);
+        double s = 0.0;
+        for (int k = lane; k < len; k += 32) {
+            const double a = (double)to_f32(vals[start + k]);
+            s += a * a;
+        }
+        best = fmax(best, warp_sum(s));
+    }
+    const double r = block_reduce(best, true);
+    if (threadIdx.x == 0) partial[blockIdx.x] = r;
+}
+
+template <typename S>
+__device__ __forceinline__ double src_to_f64(const S *p, int64_t k);
+template <> __device__ __forceinline__ double src_to_f64<double>(const double *p, int64_t k) { return p[k]; }
+template <> __device__ __forceinline__ double src_to_f64<float>(const float *p, int64_t k) { return p[k]; }
+template <> __device__ __forceinline__ double src_to_f64<__nv_bfloat16>(const __nv_bfloat16 *p, int64_t k) {
+    return (double)__bfloat162float(p[k]);
+}
+template <> __device__ __forceinline__ double src_to_f64<__half>(const __half *p, int64_t k) {
+    return (double)__half2float(p[k]);
+}
+
+template <typename D>
+__device__ __forceinline__ D from_f64(double v);
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f64<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+template <> __device__ __forceinline__ __half from_f64<__half>(double v) { return __double2half(v); }
+
+// Round-to-nearest conversion of the input values to the storage type.
+template <typename S, typename D>
+__global__ void convert_kernel(const S *src, D *dst, int64_t count) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x)
+        dst[k] = from_f64<D>(src_to_f64<S>(src, k));
+}
+
+__global__ void labels_kernel(const double *l64, float *l32, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        l32[k] = (float)l64[k];
+}
+
+// ------------------------------------------------------------------ launchers
+
+static int elementwise_grid(int64_t count) {
+    int64_t g = (count + 255) / 256;
+    if (g > 8192) g = 8192;
+    return g < 1 ? 1 : (int)g;
+}
+
+template <typename T, bool kDense>
+static void objective_rows_t(const EvalParams &p, int grid, double *partial, cudaStream_t s) {
+    objective_rows_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, partial);
+}
+
+cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
+                                  cudaStream_t s) {
+    switch (vtype) {
+    case kF32: dense ? objective_rows_t<float, true>(p, grid, partial, s) : objective_rows_t<float, false>(p, grid, partial, s); break;
+    case kBF16: dense ? objective_rows_t<__nv_bfloat16, true>(p, grid, partial, s) : objective_rows_t<__nv_bfloat16, false>(p, grid, partial, s); break;
+    case kF16: dense ? objective_rows_t<__half, true>(p, grid, partial, s) : objective_rows_t<__half, false>(p, grid, partial, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_finish(const double *partial, int grid, double inv_n, double lambda, double *out,
+                                    cudaStream_t s) {
+    objective_finish_kernel<<<1, 256, 0, s>>>(partial, grid, inv_n, lambda, out);
+    return cudaGetLastError();
+}
+
+template <typename T, bool kDense>
+static cudaError_t scatter_t(const EvalParams &p, int mode, int grid, double *acc, cudaStream_t s) {
+    if (kDense && p.d <= kSmemCols) {
+        const size_t smem = (size_t)p.d * sizeof(double);
+        scatter_rows_kernel<T, kDense, true><<<grid, kEvalBlock, smem, s>>>(p, mode, acc);
+    } else {
+        scatter_rows_kernel<T, kDense, false><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(const EvalParams &p, int vtype, bool dense, int mode, int grid, double *acc,
+                                cudaStream_t s) {
+    switch (vtype) {
+    case kF32: return dense ? scatter_t<float, true>(p, mode, grid, acc, s) : scatter_t<float, false>(p, mode, grid, acc, s);
+    case kBF16: return dense ? scatter_t<__nv_bfloat16, true>(p, mode, grid, acc, s) : scatter_t<__nv_bfloat16, false>(p, mode, grid, acc, s);
+    case kF16: return dense ? scatter_t<__half, true>(p, mode, grid, acc, s) : scatter_t<__half, false>(p, mode, grid, acc, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double *acc, double *partial,
+                                 cudaStream_t s) {
+    column_finish_kernel<<<grid, kEvalBlock, 0, s>>>(p, mode, acc, partial);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out, cudaStream_t s) {
+    reduce_partials_kernel<<<1, 256, 0, s>>>(partial, grid, mode, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s) {
+    if (nnz > 0) count_columns_kernel<<<elementwise_grid(nnz), 256, 0, s>>>(col_idx, nnz, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n, cudaStream_t s) {
+    init_state_kernel<<<elementwise_grid(d), 256, 0, s>>>(state, stride, d, count, n);
+    return cudaGetLastError();
+}
+
+template <typename T, bool kDense>
+static void norm_t(const EvalParams &p, int grid, double *partial, cudaStream_t s) {
+    row_norm2_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, partial);
+}
+
+cudaError_t launch_max_row_norm2(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
+                                 double *out, cudaStream_t s) {
+    switch (vtype) {
+    case kF32: dense ? norm_t<float, true>(p, grid, partial, s) : norm_t<float, false>(p, grid, partial, s); break;
+    case kBF16: dense ? norm_t<__nv_bfloat16, true>(p, grid, partial, s) : norm_t<__nv_bfloat16, false>(p, grid, partial, s); break;
+    case kF16: dense ? norm_t<__half, true>(p, grid, partial, s) : norm_t<__half, false>(p, grid, partial, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_reduce_partials(partial, grid, 1, out, s);
+}
+
+template <typename S>
+static cudaError_t convert_from(const S *src, void *dst, int vtype, int64_t count, cudaStream_t s) {
+    const int g = elementwise_grid(count);
+    switch (vtype) {
+    case kF32: convert_kernel<S, float><<<g, 256, 0, s>>>(src, (float *)dst, count); break;
+    case kBF16: convert_kernel<S, __nv_bfloat16><<<g, 256, 0, s>>>(src, (__nv_bfloat16 *)dst, count); break;
+    case kF16: convert_kernel<S, __half><<<g, 256, 0, s>>>(src, (__half *)dst, count); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype, int64_t count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    switch (src_dtype) {
+    case 0: return convert_from((const double *)src, dst, vtype, count, s);
+    case 1: return convert_from((const float *)src, dst, vtype, count, s);
+    case 2: return convert_from((const __nv_bfloat16 *)src, dst, vtype, count, s);
+    case 3: return convert_from((const __half *)src, dst, vtype, count, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_labels(const double *lab64, float *lab32, int64_t n, cudaStream_t s) {
+    labels_kernel<<<elementwise_grid(n), 256, 0, s>>>(lab64, lab32, n);
+    return cudaGetLastError();
+}
+
+}  // namespace asaga

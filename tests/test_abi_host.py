@@ -1,0 +1,115 @@
+"""The C ABI on the host: the library loads, exports what include/asaga.h
+declares, and rejects invalid problems before touching the GPU (CPU only)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1606_04809_gb300 import asaga, build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return asaga.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = asaga.header_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_default_options(lib):
+    o = asaga.asaga_default_options()
+    assert o.loss == 0 and o.lambda_ == 0.0 and o.gamma == 0.0 and o.storage_dtype == asaga.DTYPE["f32"]
+    assert o.epochs_per_segment == 1 and o.deterministic == 0 and o.cuda_stream is None
+
+
+def test_status_strings(lib):
+    for s, name in enumerate(asaga.STATUS_NAMES):
+        assert asaga.asaga_status_string(s) == name
+    assert asaga.asaga_status_string(99) == "ASAGA_UNKNOWN"
+
+
+def small_csr():
+    row_ptr = np.array([0, 2, 3, 5], dtype=np.int64)
+    col_idx = np.array([0, 2, 1, 0, 3], dtype=np.int32)
+    values = np.array([1.0, -0.5, 2.0, 0.25, 1.0])
+    labels = np.array([1.0, -1.0, 1.0])
+    return row_ptr, col_idx, values, labels
+
+
+def create(row_ptr, col_idx, values, labels, n=3, d=4, dtype="f64", dense=False, nnz=None, **opt):
+    prob = asaga.Problem(n, d, row_ptr, col_idx, values, dtype, labels, dense=dense, nnz=nnz)
+    o = asaga.asaga_default_options(**opt)
+    ctx = ctypes.c_void_p()
+    s = asaga.load().asaga_create(ctypes.byref(ctx), ctypes.byref(prob.struct), ctypes.byref(o))
+    if ctx.value:
+        asaga.asaga_destroy(ctx.value)
+    return s, asaga.asaga_last_error(None)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda a: a[0].__setitem__(2, 1), "decreases"),
+    (lambda a: a[0].__setitem__(3, 4), "end at nnz"),
+    (lambda a: a[1].__setitem__(1, 4), "out of range"),
+    (lambda a: a[1].__setitem__(1, -1), "out of range"),
+    (lambda a: a[1].__setitem__(1, 0), "repeated column"),
+    (lambda a: a[2].__setitem__(2, np.nan), "non-finite value"),
+    (lambda a: a[2].__setitem__(2, np.inf), "non-finite value"),
+    (lambda a: a[3].__setitem__(1, 0.0), "not +-1"),
+    (lambda a: a[3].__setitem__(1, np.nan), "non-finite label"),
+])
+def test_invalid_csr_is_rejected(lib, mutate, msg):
+    arrs = list(small_csr())
+    mutate(arrs)
+    s, err = create(*arrs)
+    assert s == asaga.EINVAL and msg in err
+
+
+@pytest.mark.parametrize("opt,msg", [
+    (dict(lam=-1.0), "lambda"),
+    (dict(lam=float("nan")), "lambda"),
+    (dict(gamma=float("inf")), "gamma"),
+    (dict(storage_dtype="f64"), "storage_dtype"),
+    (dict(loss=7), "loss"),
+    (dict(max_warps=-2), "negative"),
+])
+def test_invalid_options_are_rejected(lib, opt, msg):
+    s, err = create(*small_csr(), **opt)
+    assert s == asaga.EINVAL and msg in err
+
+
+def test_invalid_shapes_are_rejected(lib):
+    rp, ci, v, y = small_csr()
+    assert create(rp, ci, v, y, n=0)[0] == asaga.EINVAL
+    assert create(rp, ci, v, y, d=0)[0] == asaga.EINVAL
+    assert create(None, ci, v, y)[0] == asaga.EINVAL
+    assert create(rp, ci, v, None)[0] == asaga.EINVAL
+    dense_vals = np.ones(12)
+    assert create(None, None, dense_vals, y, dense=True, nnz=5)[0] == asaga.EINVAL
+
+
+def test_bf16_and_f16_nonfinite_bit_patterns(lib):
+    rp, ci, _, y = small_csr()
+    bad16 = np.array([0x3C00, 0x7C00, 0x3C00, 0x3C00, 0x3C00], dtype=np.uint16)  # f16 +inf
+    assert create(rp, ci, bad16, y, dtype="f16")[0] == asaga.EINVAL
+    badbf = np.array([0x3F80, 0x3F80, 0x7FC0, 0x3F80, 0x3F80], dtype=np.uint16)  # bf16 NaN
+    assert create(rp, ci, badbf, y, dtype="bf16")[0] == asaga.EINVAL
+
+
+def test_null_context_calls(lib):
+    L = asaga.load()
+    assert L.asaga_run(None, 1.0, 0.0, 1.0, None) == asaga.EINVAL
+    assert L.asaga_objective(None, None) == asaga.EINVAL
+    L.asaga_destroy(None)  # no-op
+
+
+def test_valid_problem_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s, err = create(*small_csr())
+    assert s == asaga.ECUDA and err
