@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--warps", type=int, default=0, help="fixed concurrent warps (skips the autotuner)")
+    ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
     return ap.parse_args()
 
 
@@ -225,6 +227,7 @@ def run_reference(args, p, wl):
 
 # ---------------------------------------------------------------- our arm
 
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -259,7 +262,19 @@ def main():
 
     opts = dict(seed=1000 + rank, abar_recompute_every=ABAR_EVERY, cuda_stream=stream.cuda_stream)
     ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
+    # schedule: concurrent warps and step size picked by the native autotuner
+    if args.warps > 0:
+        L = asaga.asaga_get_info(ctx.ctx)["L"]
+        ctx.close()
+        opts.update(max_warps=args.warps, gamma=args.gamma_scale / (3.0 * L))
+        ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
+        tune = {"fixed": True, "warps": args.warps, "gamma_scale": args.gamma_scale}
+    else:
+        t_tune = time.perf_counter()
+        tune = asaga.asaga_autotune(ctx.ctx)
+        tune["wall_seconds"] = time.perf_counter() - t_tune
     info = asaga.asaga_get_info(ctx.ctx)
+    opts.update(max_warps=info["warps"], gamma=info["gamma"])
 
     for _ in range(args.warmup):
         asaga.asaga_run(ctx.ctx, 1)
@@ -356,6 +371,7 @@ def main():
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_target": ttt,
+            "autotune": tune,
             "e2e": e2e,
             "roofline": roofline,
             "cpu_baseline": cpu,

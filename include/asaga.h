@@ -15,7 +15,7 @@
  * where x^ is the (inconsistent) value read for the dot product and
  * D_v = n / |{i : v in S_i}| (Sec. 2), 0 for columns that no row touches.
  * Many GPU warps run this update concurrently without locks; the adds to x
- * and abar are atomic (Sec. 3.2, Property "atomicity").
+ * and abar are atomic (Sec. 3.3, Property "atomicity").
  *
  * Conventions for every entry point:
  *   - the library owns all device state; it copies the problem at create
@@ -136,12 +136,21 @@ typedef struct {
     int64_t n, d, nnz;
     double L;            /* c max_i |a_i|^2 + lambda, on the stored values      */
     double gamma;        /* step size in use                                    */
-    double delta;        /* max_v |{i : v in S_i}| / n (Sec. 3.3, "Sparsity")   */
+    double delta;        /* max_v |{i : v in S_i}| / n (Sec. 3.4, "Sparsity")   */
     int warps;           /* concurrent solver warps of asaga_run                */
     int column_stride;   /* per-column state spacing in 16-byte units           */
     int64_t device_bytes;/* device memory held by the context                   */
     int64_t max_row_len; /* longest row                                          */
 } asaga_info;
+
+/* Outcome of asaga_autotune. */
+typedef struct {
+    int warps;           /* chosen number of concurrent solver warps            */
+    double gamma;        /* chosen step size                                    */
+    double score;        /* decrease of ln |grad f|^2 per device second          */
+    int trials;          /* (warps, gamma) pairs tried                          */
+    double seconds;      /* device time spent in the trials                      */
+} asaga_tune_result;
 
 /* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
  * automatic warps, asynchronous, seed 0, 1 epoch per segment, no abar
@@ -168,6 +177,21 @@ asaga_status asaga_create(asaga_ctx **out, const asaga_problem *problem,
  * res may be NULL. */
 asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subopt,
                        double f_star, asaga_result *res);
+
+/* Picks the number of concurrent warps and the step size for asaga_run.
+ * The overlap tau of asynchronous updates grows with the number of warps,
+ * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)),
+ * so this runs short trials -- trial_epochs epochs each (<= 0: 6) from
+ * x = 0, alpha = 0 -- starting at the resident maximum of warps (at most
+ * n/4) and halving down to 32, with steps gamma0 * 2^(-k/2) (gamma0 =
+ * options.gamma or 1/(3L)).  For each warp count it keeps the largest step
+ * under which the float64 |grad f|^2 decreases monotonically over the last
+ * two trial epochs, scores it by the decrease of ln |grad f|^2 per device
+ * second, and stops once the score has peaked.  The chosen step is 0.7x the
+ * largest stable one (a margin for runs longer than a trial).  Leaves the
+ * state at x = 0, alpha = 0, abar = 0 (sampler position 0) with the chosen
+ * pair in use.  EINVAL in deterministic mode. */
+asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);
 
 /* Deterministic replay: runs one update per entry of idx (row indices in
  * [0,n)), strictly in order, on a single warp.  idx is a host pointer if

@@ -138,7 +138,7 @@ def reweighting(p) -> np.ndarray:
 
 
 def sparsity_delta(p) -> float:
-    """Delta = max_v |{i : v in S_i}| / n (Sec. 3.3, Definition 'Sparsity')."""
+    """Delta = max_v |{i : v in S_i}| / n (Sec. 3.4, Definition 'Sparsity')."""
     return float(column_counts(p).max() / p.n)
 
 
@@ -203,7 +203,7 @@ def abar_from_scratch(p, alpha: np.ndarray) -> np.ndarray:
 def dense_saga_step(p, state: State, i: int, gamma: float) -> State:
     """One step of the original, dense SAGA update (Eq. SAGAupdate) in place:
     x+ = x - gamma (f'_i(x) - alpha_i a_i + abar) with f'_i(x) = phi'_i a_i +
-    lambda x, i.e. the data term remembered as the scalar alpha_i (App. E.2)
+    lambda x, i.e. the data term remembered as the scalar alpha_i (App. G.2)
     and the l2 term's gradient taken exactly and unprojected.  This is the
     D = I counterpart of the Sec. 4.2 update; it serves only to check the
     sparse variant against it."""

@@ -13,7 +13,7 @@
  *   - with the l2 term projected the same way, Sec. 4.2 "Exact
  *     regularization":  x+ = x - gamma (f'_i(x) - alpha_i + D_i abar + lambda D_i x);
  *   - for linear models f_i(x) = phi_i(a_i.x) the memory alpha_i is the scalar
- *     phi'_i at the last visit (App. E.2 "Efficient storage of the alpha_i"),
+ *     phi'_i at the last visit (App. G.2 "Efficient storage of the alpha_i"),
  *     so the vector gradient memory is alpha_i a_i and
  *     abar = (1/n) sum_i alpha_i a_i (Sec. 2, definition after Eq. SAGAupdate);
  *   - abar is kept up to date online (Algorithm 2): after the x update,

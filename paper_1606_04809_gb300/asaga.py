@@ -70,6 +70,14 @@ class asaga_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class asaga_tune_result(ctypes.Structure):
+    _fields_ = [("warps", ctypes.c_int), ("gamma", ctypes.c_double), ("score", ctypes.c_double),
+                ("trials", ctypes.c_int), ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -95,6 +103,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_create.argtypes = [P(vp), P(asaga_problem), P(asaga_options)]
     L.asaga_run.argtypes = [vp, dbl, dbl, dbl, P(asaga_result)]
     L.asaga_run_indices.argtypes = [vp, vp, i64, i32]
+    L.asaga_autotune.argtypes = [vp, dbl, P(asaga_tune_result)]
     L.asaga_objective.argtypes = [vp, P(dbl)]
     L.asaga_full_grad.argtypes = [vp, vp, P(dbl)]
     L.asaga_recompute_abar.argtypes = [vp, P(dbl)]
@@ -107,7 +116,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_status_string.restype = ctypes.c_char_p
     L.asaga_destroy.argtypes = [vp]
     L.asaga_destroy.restype = None
-    for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_objective", "asaga_full_grad",
+    for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_autotune", "asaga_objective", "asaga_full_grad",
               "asaga_recompute_abar", "asaga_get_state", "asaga_set_state", "asaga_get_info"):
         getattr(L, f).restype = i32
     _lib = L
@@ -195,6 +204,12 @@ def asaga_run(ctx: int, max_epochs: float, target_rel_subopt: float = 0.0, f_sta
     if s in (EINVAL, ENOMEM, ECUDA):
         raise AsagaError(s, asaga_last_error(ctx))
     return s, r
+
+
+def asaga_autotune(ctx: int, trial_epochs: float = 0.0) -> dict:
+    r = asaga_tune_result()
+    _check(ctx, load().asaga_autotune(ctx, float(trial_epochs), ctypes.byref(r)))
+    return r.as_dict()
 
 
 def asaga_run_indices(ctx: int, idx, on_device: bool = False) -> None:

@@ -29,6 +29,8 @@ struct asaga_ctx {
     double lambda = 0, gamma = 0, L = 0, delta = 0;
     int stride = 1;
     int warps = 1;
+    int resident_warps = 1;
+    double gamma_base = 0;  // options.gamma, or 1/(3L)
     bool deterministic = false;
     uint64_t seed = 0;
     int epochs_per_segment = 1;
@@ -51,6 +53,9 @@ struct asaga_ctx {
     double *partial = nullptr;
     double *dout = nullptr;  // [0] f, [1..] small results
     int *status = nullptr;
+    int *hot_slot = nullptr;  // d: shared-memory slot of a frequent column or -1
+    int *hot_col = nullptr;   // n_hot: column of each slot
+    int n_hot = 0;
     int64_t *idx_buf = nullptr;
     int64_t idx_cap = 0;
     double *hout = nullptr;  // pinned mirror of dout
@@ -225,6 +230,9 @@ EvalParams eval_params(const asaga_ctx *c) {
     e.stride = c->stride;
     e.loss = c->loss;
     e.lambda = c->lambda;
+    e.hot_slot = c->hot_slot;
+    e.hot_col = c->hot_col;
+    e.n_hot = c->n_hot;
     return e;
 }
 
@@ -252,6 +260,27 @@ asaga_status enqueue_recompute(asaga_ctx *c, std::string *err) {
 asaga_status stream_sync(asaga_ctx *c, std::string *err) {
     CK(cudaStreamSynchronize(c->stream), "stream synchronize");
     return ASAGA_OK;
+}
+
+// The most frequent columns (at most kMaxHot, each in at least n/4096 rows)
+// get a per-block shared-memory accumulator in the float64 A^T w scatters.
+asaga_status select_hot_columns(asaga_ctx *c, const std::vector<int> &count, std::string *err) {
+    const int64_t floor_count = std::max<int64_t>(64, c->n / 4096);
+    std::vector<int> cand;
+    for (int64_t v = 0; v < c->d; ++v)
+        if (count[v] >= floor_count) cand.push_back((int)v);
+    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return count[a] != count[b] ? count[a] > count[b] : a < b; });
+    if ((int)cand.size() > kMaxHot) cand.resize(kMaxHot);
+    c->n_hot = (int)cand.size();
+    if (c->n_hot == 0) return ASAGA_OK;
+    std::vector<int> slot(c->d, -1);
+    for (int s = 0; s < c->n_hot; ++s) slot[cand[s]] = s;
+    TRY(dev_alloc(&c->hot_slot, c->d, c, err, "alloc hot slots"));
+    TRY(dev_alloc(&c->hot_col, c->n_hot, c, err, "alloc hot columns"));
+    CK(cudaMemcpyAsync(c->hot_slot, slot.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy slots");
+    CK(cudaMemcpyAsync(c->hot_col, cand.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "copy hot columns");
+    return stream_sync(c, err);
 }
 
 asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
@@ -370,6 +399,7 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
         int mx = 0;
         for (int v : count_h) mx = v > mx ? v : mx;
         c->delta = (double)mx / (double)c->n;
+        TRY(select_hot_columns(c, count_h, err));
     }
 
     // concurrency: resident warps of the update kernel, bounded by n so that
@@ -380,6 +410,8 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     if (w > resident) w = resident;
     if (c->deterministic) w = 1;
     c->warps = (int)w;
+    c->resident_warps = (int)resident;
+    c->gamma_base = c->gamma;
     return ASAGA_OK;
 }
 
@@ -398,6 +430,8 @@ void release(asaga_ctx *c) {
     cudaFree(c->dout);
     cudaFree(c->status);
     cudaFree(c->idx_buf);
+    cudaFree(c->hot_slot);
+    cudaFree(c->hot_col);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstatus) cudaFreeHost(c->hstatus);
     for (auto &ev : c->ev)
@@ -523,6 +557,128 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
     return st;
 }
 
+asaga_status reset_state(asaga_ctx *c, std::string *err) {
+    CK(cudaMemsetAsync(c->alpha, 0, c->n * sizeof(float), c->stream), "memset alpha");
+    CK(cudaMemset2DAsync(c->state, (size_t)c->stride * sizeof(float4), 0, 2 * sizeof(float), c->d, c->stream),
+       "memset state");
+    c->updates_done = 0;
+    return ASAGA_OK;
+}
+
+asaga_status enqueue_grad(asaga_ctx *c, std::string *err) {
+    const EvalParams e = eval_params(c);
+    CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
+    CK(launch_scatter_rows(e, c->vtype, c->dense, 0, c->eval_grid, c->acc64, c->stream), "gradient scatter");
+    CK(launch_column_finish(e, 0, c->eval_grid, c->acc64, c->partial, c->stream), "gradient finish");
+    CK(launch_reduce_partials(c->partial, c->eval_grid, 0, c->dout + 2, c->stream), "gradient reduce");
+    c->launches += 3;
+    return ASAGA_OK;
+}
+
+// One epoch of updates with the given warps and step; returns the update
+// kernel's device time and |grad f|^2 after it.
+asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, double *g2, std::string *err) {
+    UpdateParams u = update_params(c);
+    u.nwarps = warps;
+    u.fence_each = warps == 1;
+    u.gamma = (float)gamma;
+    u.t_begin = (uint64_t)c->updates_done;
+    u.count = c->n;
+    CK(cudaEventRecord(c->ev[0], c->stream), "event");
+    TRY(launch_updates(c, u, err));
+    CK(cudaEventRecord(c->ev[1], c->stream), "event");
+    c->updates_done += c->n;
+    if (g2) {
+        TRY(enqueue_grad(c, err));
+        CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
+    }
+    TRY(stream_sync(c, err));
+    float f = 0;
+    cudaEventElapsedTime(&f, c->ev[0], c->ev[1]);
+    *ms = f;
+    if (g2) *g2 = c->hout[2];
+    return ASAGA_OK;
+}
+
+asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
+    if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
+    if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int E = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 6;
+    // warp counts, largest first: the resident maximum (bounded by n/4), then halvings down to 32
+    std::vector<int> cands;
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
+    cands.push_back((int)cap);
+    int64_t w = 1;
+    while (w * 2 < cap) w *= 2;
+    for (; w >= 32; w /= 2)
+        if (w < cap) cands.push_back((int)w);
+    // step scales: powers of 2^-1/2
+    std::vector<double> scales;
+    for (int k = 0; k <= 12; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
+    const double kMargin = 0.7;  // the step used is 0.7x the largest one found stable in a trial
+    asaga_tune_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.warps = c->warps;
+    r.gamma = c->gamma_base;
+    r.score = -1.0;
+    TRY(reset_state(c, err));
+    TRY(enqueue_grad(c, err));
+    CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
+    TRY(stream_sync(c, err));
+    const double g0 = c->hout[2];
+    size_t first_scale = 0;
+    double best_scale = 0;
+    for (int W : cands) {
+        bool found = false;
+        for (size_t k = first_scale; k < scales.size(); ++k) {
+            const double gamma = c->gamma_base * scales[k];
+            TRY(reset_state(c, err));
+            double g[3] = {g0, g0, g0};
+            double t_ms = 0;
+            bool ok = true;
+            for (int e = 1; e <= E; ++e) {
+                double ms = 0, g2 = g0;
+                TRY(trial_epoch(c, W, gamma, &ms, e >= E - 2 ? &g2 : nullptr, err));
+                t_ms += ms;
+                if (e >= E - 2) {
+                    g[e - (E - 2)] = g2;
+                    if (!std::isfinite(g2) || g2 > 1e6 * g0) {
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            ++r.trials;
+            r.seconds += t_ms * 1e-3;
+            const bool stable = ok && g[2] <= g[1] && g[1] <= g[0] && g[2] < g0;
+            if (!stable) continue;
+            found = true;
+            const double score = std::log(g0 / g[2]) / (t_ms * 1e-3);
+            if (score > r.score) {
+                r.score = score;
+                r.warps = W;
+                best_scale = scales[k];
+            }
+            // halving the warps roughly halves the overlap: start one notch above next time
+            first_scale = k >= 2 ? k - 2 : 0;
+            break;
+        }
+        if (found && r.score > 0 && r.warps != W) {
+            // past the best warp count: stop once the score has clearly dropped
+            if (W < r.warps / 2) break;
+        }
+    }
+    if (r.score > 0) r.gamma = c->gamma_base * best_scale * kMargin;
+    TRY(reset_state(c, err));
+    if (r.score > 0) {
+        c->warps = r.warps;
+        c->gamma = r.gamma;
+    }
+    if (res) *res = r;
+    return ASAGA_OK;
+}
+
 asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, int on_device, std::string *err) {
     if (count < 0) return fail(err, ASAGA_EINVAL, "count < 0");
     if (count == 0) return ASAGA_OK;
@@ -536,6 +692,8 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
             CK(cudaStreamSynchronize(c->stream), "sync");
             if (c->idx_buf) {
                 cudaFree(c->idx_buf);
+    cudaFree(c->hot_slot);
+    cudaFree(c->hot_col);
                 c->device_bytes -= c->idx_cap * (int64_t)sizeof(int64_t);
                 c->idx_buf = nullptr;
                 c->idx_cap = 0;
@@ -607,6 +765,11 @@ asaga_status asaga_run(asaga_ctx *c, double max_epochs, double target, double f_
     return run_impl(c, max_epochs, target, f_star, res, &c->err);
 }
 
+asaga_status asaga_autotune(asaga_ctx *c, double trial_epochs, asaga_tune_result *res) {
+    if (!c) return ASAGA_EINVAL;
+    return autotune_impl(c, trial_epochs, res, &c->err);
+}
+
 asaga_status asaga_run_indices(asaga_ctx *c, const int64_t *idx, int64_t count, int idx_on_device) {
     if (!c) return ASAGA_EINVAL;
     return run_indices_impl(c, idx, count, idx_on_device, &c->err);
@@ -627,12 +790,7 @@ asaga_status asaga_full_grad(asaga_ctx *c, double *grad, double *norm2) {
     if (!c) return ASAGA_EINVAL;
     std::string *err = &c->err;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const EvalParams e = eval_params(c);
-    CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
-    CK(launch_scatter_rows(e, c->vtype, c->dense, 0, c->eval_grid, c->acc64, c->stream), "gradient scatter");
-    CK(launch_column_finish(e, 0, c->eval_grid, c->acc64, c->partial, c->stream), "gradient finish");
-    CK(launch_reduce_partials(c->partial, c->eval_grid, 0, c->dout + 2, c->stream), "gradient reduce");
-    c->launches += 3;
+    TRY(enqueue_grad(c, err));
     CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy norm");
     if (grad) CK(cudaMemcpyAsync(grad, c->acc64, c->d * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy grad");
     TRY(stream_sync(c, err));

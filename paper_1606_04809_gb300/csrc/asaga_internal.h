@@ -51,11 +51,15 @@ struct EvalParams {
     int stride;
     int loss;
     double lambda;
+    const int *hot_slot;      // d entries: shared-memory slot of a frequent column, -1 otherwise (may be nullptr)
+    const int *hot_col;       // n_hot entries: column of each slot
+    int n_hot;
 };
 
 constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
 constexpr int kEvalBlock = 256;
 constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
+constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in shared memory
 
 // update.cu
 cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,

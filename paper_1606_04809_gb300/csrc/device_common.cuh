@@ -23,6 +23,10 @@ template <typename T> __device__ __forceinline__ T ld_stream(const T *p) { retur
 // atomics other SMs apply).
 __device__ __forceinline__ float4 ld_state(const float4 *p) { return __ldcg(p); }
 
+// Read of state that no thread writes during the kernel (evaluations):
+// L1-cached, non-coherent path.
+__device__ __forceinline__ float4 ld_state_ro(const float4 *p) { return __ldg(p); }
+
 // x_v += dx and abar_v += dab as one vector reduction at L2 (each element
 // is added atomically; nothing is returned).
 __device__ __forceinline__ void red_add_v2(float4 *p, float dx, float dab) {

@@ -7,7 +7,10 @@
 //                  max_i |a_i|^2 for L, value conversion to the storage type.
 //
 // All sums run in float64 on float32 state and stored values widened
-// exactly.  Row sums use one warp per row (grid-stride); block results go to
+// exactly.  Nothing writes the state while a row kernel runs, so x is read
+// through the L1-cached read-only path: the most frequent columns, which
+// appear in nearly every row, are then served by each SM's L1 instead of
+// serialising at one L2 line.  Row sums use one warp per row (grid-stride); block results go to
 // a partial array reduced by a single block in a fixed order, so objective
 // values are bitwise reproducible.  Column scatters (A^T w) use float64
 // atomics at L2; on dense problems with few columns each block first
@@ -25,7 +28,7 @@ __device__ __forceinline__ double row_dot(const EvalParams &P, const T *vals, in
     double z = 0.0;
     for (int k = lane; k < len; k += 32) {
         const int c = dense ? k : __ldg(P.col_idx + start + k);
-        z += (double)to_f32(vals[start + k]) * (double)ld_state(P.state + (int64_t)c * P.stride).x;
+        z += (double)to_f32(vals[start + k]) * (double)ld_state_ro(P.state + (int64_t)c * P.stride).x;
     }
     return warp_sum(z);
 }
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalPa
     }
     double xx = 0.0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.d; v += (int64_t)gridDim.x * blockDim.x) {
-        const double xv = ld_state(P.state + v * P.stride).x;
+        const double xv = ld_state_ro(P.state + v * P.stride).x;
         xx += xv * xv;
     }
     const double s1 = block_reduce(acc, false);
@@ -99,7 +102,11 @@ __global__ void objective_finish_kernel(const double *partial, int grid, double 
 }
 
 // acc[v] += sum_i w_i a_iv, w_i = phi'_i(a_i.x)/n (mode 0) or alpha_i/n (mode 1).
-template <typename T, bool kDense, bool kSmem>
+// kSlots: 0 = every column goes straight to a float64 atomic at L2;
+//         1 = dense rows, all d columns accumulate per block in shared memory;
+//         2 = the n_hot most frequent columns accumulate per block in shared
+//             memory (their atomics would otherwise serialise at one L2 line).
+template <typename T, bool kDense, int kSlotsMode>
 __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalParams P, int mode, double *acc) {
     extern __shared__ double sacc[];
     const T *vals = static_cast<const T *>(P.values);
@@ -108,8 +115,9 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
     const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
     const int64_t tw = (int64_t)gridDim.x * wpb;
     const double inv_n = 1.0 / (double)P.n;
-    if (kSmem) {
-        for (int v = threadIdx.x; v < P.d; v += blockDim.x) sacc[v] = 0.0;
+    const int nslots = kSlotsMode == 1 ? (int)P.d : (kSlotsMode == 2 ? P.n_hot : 0);
+    if (kSlotsMode) {
+        for (int v = threadIdx.x; v < nslots; v += blockDim.x) sacc[v] = 0.0;
         __syncthreads();
     }
     for (int64_t i = gw; i < P.n; i += tw) {
@@ -126,15 +134,17 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
         for (int k = lane; k < len; k += 32) {
             const int c = kDense ? k : __ldg(P.col_idx + start + k);
             const double contrib = w * (double)to_f32(vals[start + k]);
-            if (kSmem)
-                atomicAdd(sacc + c, contrib);
+            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);
+            if (slot >= 0)
+                atomicAdd(sacc + slot, contrib);
             else
                 atomicAdd(acc + c, contrib);
         }
     }
-    if (kSmem) {
+    if (kSlotsMode) {
         __syncthreads();
-        for (int v = threadIdx.x; v < P.d; v += blockDim.x) atomicAdd(acc + v, sacc[v]);
+        for (int v = threadIdx.x; v < nslots; v += blockDim.x)
+            atomicAdd(acc + (kSlotsMode == 1 ? v : P.hot_col[v]), sacc[v]);
     }
 }
 
@@ -264,10 +274,11 @@ cudaError_t launch_objective_finish(const double *partial, int grid, double inv_
 template <typename T, bool kDense>
 static cudaError_t scatter_t(const EvalParams &p, int mode, int grid, double *acc, cudaStream_t s) {
     if (kDense && p.d <= kSmemCols) {
-        const size_t smem = (size_t)p.d * sizeof(double);
-        scatter_rows_kernel<T, kDense, true><<<grid, kEvalBlock, smem, s>>>(p, mode, acc);
+        scatter_rows_kernel<T, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
+    } else if (!kDense && p.n_hot > 0 && p.hot_slot) {
+        scatter_rows_kernel<T, kDense, 2><<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, mode, acc);
     } else {
-        scatter_rows_kernel<T, kDense, false><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
+        scatter_rows_kernel<T, kDense, 0><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
     }
     return cudaGetLastError();
 }

@@ -2,21 +2,30 @@
 // with the projected l2 term of Sec. 4.2).
 //
 // Each warp is one ASAGA "core".  Update t of a launch samples its row
-// i = sample_row(seed, t) before reading anything (Algorithm 2: sample, then
-// read), reads x^ and abar on S_i inconsistently (other warps keep adding to
-// them), forms delta = phi'_i(a_i.x^) - alpha_i, and applies
-//     x_v += -gamma (delta a_iv + D_v (abar_v + lambda x^_v)),
-//     abar_v += delta a_iv / n,           for v in S_i,
-// as one vector atomic add per column at L2.  The memory alpha_i is swapped
-// atomically (atomicExch) and delta is taken against the value it replaced,
-// so abar = (1/n) sum_i alpha_i a_i holds in exact arithmetic even when two
-// warps visit the same row at once.
+// i = sample_row(seed, t) before reading anything (Algorithm 2 samples, then
+// reads), reads x^, abar and D on S_i and the memory alpha^_i
+// inconsistently (other warps keep adding to them), forms
+//     delta = phi'_i(a_i.x^) - alpha^_i,
+// and adds, atomically at L2,
+//     x_v    += -gamma (delta a_iv + D_v (abar_v + lambda x^_v)),
+//     abar_v += delta a_iv / n              for v in S_i,
+//     alpha_i += delta                      (Algorithm 2 increments alpha_i by delta-alpha).
+// Because alpha_i and abar receive exactly matching increments,
+// abar = (1/n) sum_i alpha_i a_i holds in exact arithmetic under any
+// interleaving of warps.
+//
+// Latency: the CSR slice of a row does not depend on the solver state, so a
+// warp loads the column indices and values of its next two rows (and the
+// row_ptr entries of the third) while it processes the current one; the
+// window between reading x^ and writing x, which sets the overlap tau, is
+// then one L2 gather, a warp reduction and the reductions back to L2.
 //
 // Layout: A in CSR (int64 row_ptr, int32 col_idx, values in fp32/bf16/fp16)
-// or dense row-major; per-column state float4 {x, abar, D, 0} so that one
-// 16-byte L2 read serves x^_v, abar_v and D_v.  Row elements are spread over
-// the 32 lanes; up to 32 * kSlots elements stay in registers between the
-// dot product and the scatter; the rest of a longer row is read again.
+// or dense row-major; per-column state float4 {x, abar, D, 0}, so one
+// 16-byte L2 read serves x^_v, abar_v and D_v and one 8-byte vector
+// reduction updates x_v and abar_v.  Up to 32 * kSlots entries of a row are
+// held in registers (lane l owns entries l, l+32, ...); longer rows read
+// the remainder again from memory.
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -24,113 +33,160 @@ namespace asaga {
 
 constexpr int kSlots = 4;
 
-template <typename T, bool kDense>
-__device__ __forceinline__ void update_row(const UpdateParams &P, const T *__restrict__ vals, int64_t i,
-                                           int lane) {
+// The part of a row that does not depend on the solver state.
+struct RowData {
     int64_t start;
     int len;
-    if (kDense) {
-        start = i * P.d;
-        len = (int)P.d;
-    } else {
-        start = __ldg(P.row_ptr + i);
-        len = (int)(__ldg(P.row_ptr + i + 1) - start);
-    }
-    const float b = __ldg(P.labels + i);
-    const float4 *__restrict__ state = P.state;
-    const int64_t stride = P.stride;
-
+    float label;
     int c[kSlots];
     float a[kSlots];
-    float4 s[kSlots];
+};
+
+__device__ __forceinline__ void red_add_f32(float *p, float v) {
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+
+template <bool kDense>
+__device__ __forceinline__ void load_meta(const UpdateParams &P, int64_t i, RowData &r) {
+    if (kDense) {
+        r.start = i * P.d;
+        r.len = (int)P.d;
+    } else {
+        const int64_t s = __ldg(P.row_ptr + i);
+        r.start = s;
+        r.len = (int)(__ldg(P.row_ptr + i + 1) - s);
+    }
+    r.label = __ldg(P.labels + i);
+}
+
+template <typename T, bool kDense>
+__device__ __forceinline__ void load_slots(const UpdateParams &P, const T *__restrict__ vals, RowData &r,
+                                           int lane) {
 #pragma unroll
-    for (int r = 0; r < kSlots; ++r) {
-        const int k = lane + 32 * r;
-        c[r] = 0;
-        a[r] = 0.f;
-        if (k < len) {
-            c[r] = kDense ? k : ld_stream(P.col_idx + start + k);
-            a[r] = to_f32(ld_stream(vals + start + k));
+    for (int s = 0; s < kSlots; ++s) {
+        const int k = lane + 32 * s;
+        r.c[s] = 0;
+        r.a[s] = 0.f;
+        if (k < r.len) {
+            r.c[s] = kDense ? k : ld_stream(P.col_idx + r.start + k);
+            r.a[s] = to_f32(ld_stream(vals + r.start + k));
         }
     }
+}
+
+// Row of update t of this launch, or -1 past the end (or on a bad index).
+__device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool &bad) {
+    if (t >= P.count) return -1;
+    if (P.idx) {
+        const int64_t i = __ldg(P.idx + t);
+        if (i < 0 || i >= P.n) {
+            bad = true;
+            return -1;
+        }
+        return i;
+    }
+    return sample_row(P.seed, P.t_begin + (uint64_t)t, P.n);
+}
+
+template <typename T, bool kDense>
+__device__ __forceinline__ void process_row(const UpdateParams &P, const T *__restrict__ vals, int64_t i,
+                                            const RowData &r, int lane) {
+    const float4 *__restrict__ state = P.state;
+    const int64_t stride = P.stride;
+    float4 s[kSlots];
+#pragma unroll
+    for (int q = 0; q < kSlots; ++q) {
+        s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane + 32 * q < r.len) s[q] = ld_state(state + r.c[q] * stride);
+    }
+    const float alpha_hat = __ldcg(P.alpha + i);
     float z = 0.f;
 #pragma unroll
-    for (int r = 0; r < kSlots; ++r) {
-        const int k = lane + 32 * r;
-        s[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < len) s[r] = ld_state(state + c[r] * stride);
-    }
-#pragma unroll
-    for (int r = 0; r < kSlots; ++r) z = fmaf(a[r], s[r].x, z);
-    for (int k = lane + 32 * kSlots; k < len; k += 32) {  // rest of a long row
-        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
-        z = fmaf(to_f32(ld_stream(vals + start + k)), ld_state(state + cc * stride).x, z);
+    for (int q = 0; q < kSlots; ++q) z = fmaf(r.a[q], s[q].x, z);
+    for (int k = lane + 32 * kSlots; k < r.len; k += 32) {  // rest of a long row
+        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
+        z = fmaf(to_f32(ld_stream(vals + r.start + k)), ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
-
-    float delta = 0.f;
-    if (lane == 0) {
-        const float g = phi_prime_f32(P.loss, z, b);
-        const float old = atomicExch(P.alpha + i, g);
-        delta = g - old;
-    }
-    delta = __shfl_sync(kFull, delta, 0);
+    const float delta = phi_prime_f32(P.loss, z, r.label) - alpha_hat;  // same value in every lane
 
     const float gamma = P.gamma, lambda = P.lambda, inv_n = P.inv_n;
 #pragma unroll
-    for (int r = 0; r < kSlots; ++r) {
-        const int k = lane + 32 * r;
-        if (k < len) {
-            const float dx = -gamma * fmaf(delta, a[r], s[r].z * fmaf(lambda, s[r].x, s[r].y));
-            red_add_v2(P.state + c[r] * stride, dx, delta * a[r] * inv_n);
+    for (int q = 0; q < kSlots; ++q) {
+        if (lane + 32 * q < r.len) {
+            const float dx = -gamma * fmaf(delta, r.a[q], s[q].z * fmaf(lambda, s[q].x, s[q].y));
+            red_add_v2(P.state + r.c[q] * stride, dx, delta * r.a[q] * inv_n);
         }
     }
-    for (int k = lane + 32 * kSlots; k < len; k += 32) {
-        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
-        const float av = to_f32(ld_stream(vals + start + k));
+    for (int k = lane + 32 * kSlots; k < r.len; k += 32) {
+        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
+        const float av = to_f32(ld_stream(vals + r.start + k));
         const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
         red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
     }
+    if (lane == 0) red_add_f32(P.alpha + i, delta);
 }
 
 template <typename T, bool kDense>
-__global__ void __launch_bounds__(kUpdateBlock, 4) update_kernel(const UpdateParams P) {
+__global__ void __launch_bounds__(kUpdateBlock, 3) update_kernel(const UpdateParams P) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= P.nwarps) return;
     const T *__restrict__ vals = static_cast<const T *>(P.values);
+    const int64_t W = P.nwarps;
 
     uint64_t deadline = 0;
     if (P.deadline_ns) {  // budget relative to this warp's start (warp-uniform)
-        uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
+        const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
         deadline = now + P.deadline_ns;
     }
+    bool bad = false;
+    // software pipeline over this warp's rows: `cur` is processed while the
+    // CSR slices of the next two rows are in flight and the row_ptr entries
+    // of the third are being read
+    int64_t t = warp;
+    int64_t i_cur = row_of(P, t, bad);
+    int64_t i_n1 = i_cur >= 0 ? row_of(P, t + W, bad) : -1;
+    int64_t i_n2 = i_n1 >= 0 ? row_of(P, t + 2 * W, bad) : -1;
+    RowData cur, n1, n2;
+    if (i_cur >= 0) {
+        load_meta<kDense>(P, i_cur, cur);
+        load_slots<T, kDense>(P, vals, cur, lane);
+    }
+    if (i_n1 >= 0) {
+        load_meta<kDense>(P, i_n1, n1);
+        load_slots<T, kDense>(P, vals, n1, lane);
+    }
+    if (i_n2 >= 0) load_meta<kDense>(P, i_n2, n2);
     int64_t done = 0;
-    for (int64_t t = warp; t < P.count; t += P.nwarps) {
-        int64_t i;
-        if (P.idx) {
-            i = __ldg(P.idx + t);
-            if (i < 0 || i >= P.n) {
-                if (lane == 0) atomicOr(P.status, 2);
-                return;
-            }
-        } else {
-            i = sample_row(P.seed, P.t_begin + (uint64_t)t, P.n);
-        }
-        update_row<T, kDense>(P, vals, i, lane);
+    while (i_cur >= 0) {
+        const int64_t i_n3 = i_n2 >= 0 ? row_of(P, t + 3 * W, bad) : -1;
+        RowData n3;
+        if (i_n2 >= 0) load_slots<T, kDense>(P, vals, n2, lane);
+        if (i_n3 >= 0) load_meta<kDense>(P, i_n3, n3);
+
+        process_row<T, kDense>(P, vals, i_cur, cur, lane);
         if (P.fence_each) {
             __threadfence();
             __syncwarp();
         }
-        if (deadline && ((++done & 63) == 0)) {
+        if (deadline && ((++done & 31) == 0)) {
             const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
             if (now > deadline) {
                 if (lane == 0) atomicOr(P.status, 1);
                 return;
             }
         }
+        t += W;
+        i_cur = i_n1;
+        cur = n1;
+        i_n1 = i_n2;
+        n1 = n2;
+        i_n2 = i_n3;
+        n2 = n3;
     }
+    if (bad && lane == 0) atomicOr(P.status, 2);
 }
 
 template <typename T, bool kDense>

@@ -6,7 +6,7 @@ the CUDA path and the CPU checker can consume the same inputs without sharing
 any of the method.
 
 The shapes follow the workloads of the paper's experiments (Sec. 4.1 and the
-dataset tables of App. D.2): an RCV1-like sparse logistic problem, a URL-like
+dataset table of App. E.2): an RCV1-like sparse logistic problem, a URL-like
 very sparse high-dimensional one with binary row-normalised features, and a
 Covtype-like dense low-dimensional one (used here as a ridge problem). The
 datasets themselves are not available; every generator here is a seeded

@@ -224,11 +224,25 @@ def test_async_rcv1_shaped_medium_reaches_1e6():
     p = synth.rcv1_like(seed=22, n=60000, d=6000)
     cert = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 30, ep), rel_tol=1e-10)
     with asaga.Context(p, seed=2, abar_recompute_every=5) as c:
+        tune = asaga.asaga_autotune(c.ctx)
         s, r = asaga.asaga_run(c.ctx, 200, 1e-6, cert["fstar"])
         info = asaga.asaga_get_info(c.ctx)
         x = asaga.asaga_get_state(c.ctx)[0]
-    assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict(), info)
+    assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict(), info, tune)
+    assert info["warps"] == tune["warps"] and info["gamma"] == tune["gamma"]
     assert R.objective(p, x.astype(np.float64)) - cert["fstar"] <= 1e-6 * abs(cert["fstar"]) + cert["bound"]
+
+
+def test_autotune_leaves_a_zero_state_and_rejects_deterministic_mode():
+    p = synth.small_logistic()
+    with asaga.Context(p, seed=3) as c:
+        tune = asaga.asaga_autotune(c.ctx, 4)
+        assert tune["trials"] >= 1 and tune["warps"] >= 1 and tune["gamma"] > 0
+        x, abar, alpha = asaga.asaga_get_state(c.ctx)
+        assert not x.any() and not abar.any() and not alpha.any()
+    with asaga.Context(p, deterministic=1) as c:
+        with pytest.raises(asaga.AsagaError):
+            asaga.asaga_autotune(c.ctx)
 
 
 def test_async_dense_ridge_reaches_closed_form():
@@ -236,6 +250,7 @@ def test_async_dense_ridge_reaches_closed_form():
     xs = R.ridge_closed_form(p)
     fstar = R.objective(p, xs)
     with asaga.Context(p, seed=4, abar_recompute_every=5) as c:
+        asaga.asaga_autotune(c.ctx)
         s, r = asaga.asaga_run(c.ctx, 300, 1e-6, fstar)
         x = asaga.asaga_get_state(c.ctx)[0]
     assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict())
@@ -244,13 +259,15 @@ def test_async_dense_ridge_reaches_closed_form():
 
 
 def test_async_untouched_columns_stay_zero():
-    p = synth.sparse_logistic(5000, 3000, k_mean=8, k_min=1, k_max=20, zipf_s=None, storage="f32", seed=24)
+    p = synth.sparse_logistic(5000, 2900, k_mean=8, k_min=1, k_max=20, zipf_s=None, storage="f32", seed=24)
+    p.d = 3000  # columns 2900..2999 exist but no row touches them
     cnt = np.bincount(p.col_idx, minlength=p.d)
-    assert (cnt == 0).any()
+    assert (cnt[2900:] == 0).all()
     with asaga.Context(p, seed=5) as c:
         asaga.asaga_run(c.ctx, 5)
         x, abar, _ = asaga.asaga_get_state(c.ctx)
     assert np.all(x[cnt == 0] == 0.0) and np.all(abar[cnt == 0] == 0.0)
+    assert np.any(x != 0.0)
 
 
 def test_run_status_paths():

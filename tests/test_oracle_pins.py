@@ -139,7 +139,7 @@ def test_reweighting_counts_rows():
 
 
 def test_expected_projected_reweighting_is_identity():
-    # E_i[D_i 1] = 1 on every touched coordinate (App. A, Eq. apxBias)
+    # E_i[D_i 1] = 1 on every touched coordinate (App. B, Eq. apxBias)
     p = tiny_sparse(n=10, d=8, k=3, seed=13)
     D = R.reweighting(p)
     acc = np.zeros(p.d)
@@ -160,7 +160,7 @@ def one_step(p, st, i, gamma, D=None):
 @pytest.mark.parametrize("loss", ["logistic", "squared"])
 def test_sparse_step_is_unbiased(loss):
     """E_i[x+ - x] = -gamma grad f(x) over a uniform i, and equals the mean of the
-    original (dense) SAGA step (Sec. 2: E D_i abar = abar; App. A)."""
+    original (dense) SAGA step (Sec. 2: E D_i abar = abar; App. B)."""
     p = tiny_sparse(n=8, d=6, k=3, loss=loss, seed=14)
     st = consistent_state(p)
     gamma = 0.37
@@ -210,7 +210,7 @@ def test_memory_takes_the_new_derivative():
 
 def test_variance_identity():
     """E||alpha_i - D_i abar - f'_i(x*)||^2 = E||alpha_i - f'_i(x*)||^2 - abar^T D abar
-    (App. A, Eq. alphaiBarVariance), with vector memories alpha_i a_i and
+    (App. B, Eq. alphaiBarVariance), with vector memories alpha_i a_i and
     f'_i(x) = phi'_i a_i + lambda D_i x (the Sec. 4.2 split of the l2 term, whose
     mean over i is grad f)."""
     p = tiny_sparse(n=10, d=7, k=3, seed=18)
