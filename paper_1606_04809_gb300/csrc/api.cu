@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "asaga.h"
@@ -125,6 +127,37 @@ asaga_status dev_alloc(T **p, size_t count, asaga_ctx *c, std::string *err, cons
         if (s_ != ASAGA_OK) return s_;            \
     } while (0)
 
+std::mutex g_max_mutex;
+
+// Runs body(lo, hi, &error) over contiguous chunks of [0, count) on up to
+// max_threads host threads (at least min_chunk items each).  Returns false
+// with the error of the lowest failing chunk.
+template <class F>
+bool parallel_check(int64_t count, int64_t min_chunk, int max_threads, F body, std::string *msg) {
+    if (count <= 0) return true;
+    const int64_t hw = std::max<int64_t>(1, (int64_t)std::thread::hardware_concurrency());
+    const int nt = (int)std::max<int64_t>(1, std::min<int64_t>({count / std::max<int64_t>(1, min_chunk), hw,
+                                                               (int64_t)max_threads}));
+    std::vector<std::string> errs(nt);
+    if (nt == 1) {
+        body(0, count, &errs[0]);
+    } else {
+        std::vector<std::thread> th;
+        th.reserve(nt);
+        for (int t = 0; t < nt; ++t) {
+            const int64_t lo = count * t / nt, hi = count * (t + 1) / nt;
+            th.emplace_back([&, t, lo, hi] { body(lo, hi, &errs[t]); });
+        }
+        for (auto &x : th) x.join();
+    }
+    for (auto &e : errs)
+        if (!e.empty()) {
+            *msg = e;
+            return false;
+        }
+    return true;
+}
+
 // Host-side validation of the problem (copies device inputs to the host
 // first).  Fills max_row_len.
 asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *max_row_len, std::string *err) {
@@ -184,34 +217,52 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
             ci = ci_h.data();
         }
     }
-    for (int64_t i = 0; i < p->n; ++i) {
-        if (!std::isfinite(lab[i])) return fail(err, ASAGA_EINVAL, "non-finite label at row " + std::to_string(i));
-        if (o->loss == ASAGA_LOSS_LOGISTIC && lab[i] != 1.0 && lab[i] != -1.0)
-            return fail(err, ASAGA_EINVAL, "logistic label not +-1 at row " + std::to_string(i));
-    }
-    for (int64_t k = 0; k < nnz; ++k)
-        if (!value_finite(val, p->values_dtype, k))
-            return fail(err, ASAGA_EINVAL, "non-finite value at entry " + std::to_string(k));
+    std::string msg;
+    const int loss = o->loss;
+    if (!parallel_check(p->n, 1 << 16, 32, [&](int64_t lo, int64_t hi, std::string *e) {
+            for (int64_t i = lo; i < hi; ++i) {
+                if (!std::isfinite(lab[i])) return void(*e = "non-finite label at row " + std::to_string(i));
+                if (loss == ASAGA_LOSS_LOGISTIC && lab[i] != 1.0 && lab[i] != -1.0)
+                    return void(*e = "logistic label not +-1 at row " + std::to_string(i));
+            }
+        }, &msg))
+        return fail(err, ASAGA_EINVAL, msg);
+    const int vdt = p->values_dtype;
+    if (!parallel_check(nnz, 1 << 20, 32, [&](int64_t lo, int64_t hi, std::string *e) {
+            for (int64_t k = lo; k < hi; ++k)
+                if (!value_finite(val, vdt, k)) return void(*e = "non-finite value at entry " + std::to_string(k));
+        }, &msg))
+        return fail(err, ASAGA_EINVAL, msg);
     int64_t mrl = 0;
     if (p->dense) {
         mrl = p->d;
     } else {
         if (rp[0] != 0 || rp[p->n] != nnz) return fail(err, ASAGA_EINVAL, "row_ptr must start at 0 and end at nnz");
-        std::vector<int64_t> last(p->d, -1);
-        for (int64_t i = 0; i < p->n; ++i) {
-            if (rp[i + 1] < rp[i]) return fail(err, ASAGA_EINVAL, "row_ptr decreases at row " + std::to_string(i));
-            const int64_t len = rp[i + 1] - rp[i];
-            if (len > INT32_MAX) return fail(err, ASAGA_EINVAL, "row too long");
-            if (len > mrl) mrl = len;
-            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-                const int32_t c = ci[k];
-                if (c < 0 || c >= p->d)
-                    return fail(err, ASAGA_EINVAL, "column index out of range at entry " + std::to_string(k));
-                if (last[c] == i)
-                    return fail(err, ASAGA_EINVAL, "repeated column in row " + std::to_string(i));
-                last[c] = i;
-            }
-        }
+        // each thread checks a contiguous block of rows with its own column
+        // stamps (row number within the block + 1), bounded to 256 MB in all
+        const int64_t d = p->d;
+        const int max_threads = (int)std::max<int64_t>(1, std::min<int64_t>(32, (int64_t(256) << 20) / (4 * d)));
+        if (!parallel_check(p->n, 1 << 14, max_threads, [&](int64_t lo, int64_t hi, std::string *e) {
+                std::vector<uint32_t> stamp(d, 0);
+                int64_t m = 0;
+                for (int64_t i = lo; i < hi; ++i) {
+                    if (rp[i + 1] < rp[i]) return void(*e = "row_ptr decreases at row " + std::to_string(i));
+                    const int64_t len = rp[i + 1] - rp[i];
+                    if (len > INT32_MAX) return void(*e = "row too long");
+                    m = len > m ? len : m;
+                    const uint32_t tag = (uint32_t)(i - lo + 1);
+                    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                        const int32_t c = ci[k];
+                        if (c < 0 || c >= d)
+                            return void(*e = "column index out of range at entry " + std::to_string(k));
+                        if (stamp[c] == tag) return void(*e = "repeated column in row " + std::to_string(i));
+                        stamp[c] = tag;
+                    }
+                }
+                std::lock_guard<std::mutex> g(g_max_mutex);
+                mrl = m > mrl ? m : mrl;
+            }, &msg))
+            return fail(err, ASAGA_EINVAL, msg);
     }
     *max_row_len = mrl;
     return ASAGA_OK;

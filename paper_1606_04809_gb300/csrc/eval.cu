@@ -6,15 +6,19 @@
 //   set-up         column counts -> D_v = n / |{i : v in S_i}| (Sec. 2),
 //                  max_i |a_i|^2 for L, value conversion to the storage type.
 //
-// All sums run in float64 on float32 state and stored values widened
-// exactly.  Nothing writes the state while a row kernel runs, so x is read
-// through the L1-cached read-only path: the most frequent columns, which
-// appear in nearly every row, are then served by each SM's L1 instead of
-// serialising at one L2 line.  Row sums use one warp per row (grid-stride); block results go to
-// a partial array reduced by a single block in a fixed order, so objective
-// values are bitwise reproducible.  Column scatters (A^T w) use float64
-// atomics at L2; on dense problems with few columns each block first
-// accumulates in shared memory.
+// One thread evaluates one row (grid-stride over rows), so the float64
+// phi of 32 rows runs as one warp instruction.  Row sums a_i . x are
+// compensated float32 sums (about 48 significant bits) of the float32
+// state and stored values, widened to float64 per row; everything after
+// that (phi, row totals, column sums) is float64.  Nothing writes the state
+// while these kernels run, so x is read through the L1-cached read-only
+// path: the most frequent columns, which appear in nearly every row, are
+// served by each SM's L1 instead of serialising at one L2 line.  Block
+// results go to a partial array reduced by one block in a fixed order, so
+// objective values are bitwise reproducible.  Column scatters (A^T w) use
+// float64 atomics at L2; dense problems with few columns, and the most
+// frequent columns of sparse ones, first accumulate per block in shared
+// memory.
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -22,15 +26,38 @@ namespace asaga {
 
 constexpr int kSmemCols = 2048;  // dense problems up to this d accumulate per block in shared memory
 
+// Compensated ("float-float") accumulation of a_k x_k: each product is split
+// exactly into p + e with an FMA (Dekker/Ogita-Rump-Oishi TwoProduct) and
+// summed with Knuth's TwoSum into a (hi, lo) pair, giving about 48
+// significant bits on the fast float32 pipe.  GB300's float64 pipe is a
+// small fraction of its float32 rate, so the per-entry work stays in float32
+// and only per-row results are widened to float64.
+struct FF {
+    float hi = 0.f, lo = 0.f;
+};
+__device__ __forceinline__ void ff_add_product(FF &acc, float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ double ff_value(const FF &a) { return (double)a.hi + (double)a.lo; }
+
+// z_i = a_i . x for one row, by one thread (rows are split over threads so
+// that the float64 work per row runs on all 32 lanes at once).
 template <typename T>
-__device__ __forceinline__ double row_dot(const EvalParams &P, const T *vals, int64_t start, int len,
-                                          bool dense, int lane) {
-    double z = 0.0;
-    for (int k = lane; k < len; k += 32) {
+__device__ __forceinline__ double row_dot_thread(const EvalParams &P, const T *vals, int64_t start, int len,
+                                                 bool dense) {
+    FF acc;
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
         const int c = dense ? k : __ldg(P.col_idx + start + k);
-        z += (double)to_f32(vals[start + k]) * (double)ld_state_ro(P.state + (int64_t)c * P.stride).x;
+        ff_add_product(acc, to_f32(vals[start + k]), ld_state_ro(P.state + (int64_t)c * P.stride).x);
     }
-    return warp_sum(z);
+    return ff_value(acc);
 }
 
 template <typename T, bool kDense>
@@ -64,17 +91,13 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max) {
 template <typename T, bool kDense>
 __global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalParams P, double *partial) {
     const T *vals = static_cast<const T *>(P.values);
-    const int lane = threadIdx.x & 31;
-    const int64_t wpb = blockDim.x >> 5;
-    const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const int64_t tw = (int64_t)gridDim.x * wpb;
     double acc = 0.0;
-    for (int64_t i = gw; i < P.n; i += tw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t start;
         int len;
         row_range<T, kDense>(P, i, start, len);
-        const double z = row_dot<T>(P, vals, start, len, kDense, lane);
-        if (lane == 0) acc += phi_f64(P.loss, z, P.labels[i]);
+        const double z = row_dot_thread<T>(P, vals, start, len, kDense);
+        acc += phi_f64(P.loss, z, P.labels[i]);
     }
     double xx = 0.0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.d; v += (int64_t)gridDim.x * blockDim.x) {
@@ -110,28 +133,25 @@ template <typename T, bool kDense, int kSlotsMode>
 __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalParams P, int mode, double *acc) {
     extern __shared__ double sacc[];
     const T *vals = static_cast<const T *>(P.values);
-    const int lane = threadIdx.x & 31;
-    const int64_t wpb = blockDim.x >> 5;
-    const int64_t gw = blockIdx.x * wpb + (threadIdx.x >> 5);
-    const int64_t tw = (int64_t)gridDim.x * wpb;
     const double inv_n = 1.0 / (double)P.n;
     const int nslots = kSlotsMode == 1 ? (int)P.d : (kSlotsMode == 2 ? P.n_hot : 0);
     if (kSlotsMode) {
         for (int v = threadIdx.x; v < nslots; v += blockDim.x) sacc[v] = 0.0;
         __syncthreads();
     }
-    for (int64_t i = gw; i < P.n; i += tw) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t start;
         int len;
         row_range<T, kDense>(P, i, start, len);
         double w;
         if (mode == 0) {
-            const double z = row_dot<T>(P, vals, start, len, kDense, lane);
+            const double z = row_dot_thread<T>(P, vals, start, len, kDense);
             w = phi_prime_f64(P.loss, z, P.labels[i]) * inv_n;
         } else {
             w = (double)P.alpha[i] * inv_n;
         }
-        for (int k = lane; k < len; k += 32) {
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
             const int c = kDense ? k : __ldg(P.col_idx + start + k);
             const double contrib = w * (double)to_f32(vals[start + k]);
             const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);

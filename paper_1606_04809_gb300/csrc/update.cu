@@ -15,10 +15,10 @@
 // interleaving of warps.
 //
 // Latency: the CSR slice of a row does not depend on the solver state, so a
-// warp loads the column indices and values of its next two rows (and the
-// row_ptr entries of the third) while it processes the current one; the
-// window between reading x^ and writing x, which sets the overlap tau, is
-// then one L2 gather, a warp reduction and the reductions back to L2.
+// warp requests the column indices and values of a row two rows before it
+// processes it (and the row_ptr entries three rows before); the window
+// between reading x^ and writing x, which sets the overlap tau, is then one
+// L2 gather, a warp reduction and the reductions back to L2.
 //
 // Layout: A in CSR (int64 row_ptr, int32 col_idx, values in fp32/bf16/fp16)
 // or dense row-major; per-column state float4 {x, abar, D, 0}, so one
@@ -129,7 +129,7 @@ __device__ __forceinline__ void process_row(const UpdateParams &P, const T *__re
 }
 
 template <typename T, bool kDense>
-__global__ void __launch_bounds__(kUpdateBlock, 3) update_kernel(const UpdateParams P) {
+__global__ void __launch_bounds__(kUpdateBlock, 2) update_kernel(const UpdateParams P) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= P.nwarps) return;
@@ -142,31 +142,30 @@ __global__ void __launch_bounds__(kUpdateBlock, 3) update_kernel(const UpdatePar
         deadline = now + P.deadline_ns;
     }
     bool bad = false;
-    // software pipeline over this warp's rows: `cur` is processed while the
-    // CSR slices of the next two rows are in flight and the row_ptr entries
-    // of the third are being read
+    // Software pipeline over this warp's rows with four register buffers
+    // whose roles rotate by unrolling (no buffer is ever copied, so no copy
+    // waits on a load in flight): in each step the row in X is processed,
+    // Y's CSR slice is in flight since the previous step, Z's slice is
+    // requested (its row_ptr entries arrived during the previous step) and
+    // V's row_ptr entries are requested.
     int64_t t = warp;
-    int64_t i_cur = row_of(P, t, bad);
-    int64_t i_n1 = i_cur >= 0 ? row_of(P, t + W, bad) : -1;
-    int64_t i_n2 = i_n1 >= 0 ? row_of(P, t + 2 * W, bad) : -1;
-    RowData cur, n1, n2;
-    if (i_cur >= 0) {
-        load_meta<kDense>(P, i_cur, cur);
-        load_slots<T, kDense>(P, vals, cur, lane);
-    }
-    if (i_n1 >= 0) {
-        load_meta<kDense>(P, i_n1, n1);
-        load_slots<T, kDense>(P, vals, n1, lane);
-    }
-    if (i_n2 >= 0) load_meta<kDense>(P, i_n2, n2);
+    RowData rA, rB, rC, rD;
+    int64_t iA = row_of(P, t, bad);
+    int64_t iB = iA >= 0 ? row_of(P, t + W, bad) : -1;
+    int64_t iC = iB >= 0 ? row_of(P, t + 2 * W, bad) : -1;
+    int64_t iD = -1;
+    if (iA >= 0) load_meta<kDense>(P, iA, rA);
+    if (iB >= 0) load_meta<kDense>(P, iB, rB);
+    if (iC >= 0) load_meta<kDense>(P, iC, rC);
+    if (iA >= 0) load_slots<T, kDense>(P, vals, rA, lane);
+    if (iB >= 0) load_slots<T, kDense>(P, vals, rB, lane);
     int64_t done = 0;
-    while (i_cur >= 0) {
-        const int64_t i_n3 = i_n2 >= 0 ? row_of(P, t + 3 * W, bad) : -1;
-        RowData n3;
-        if (i_n2 >= 0) load_slots<T, kDense>(P, vals, n2, lane);
-        if (i_n3 >= 0) load_meta<kDense>(P, i_n3, n3);
-
-        process_row<T, kDense>(P, vals, i_cur, cur, lane);
+    bool stop = false;
+    auto step = [&](int64_t iX, const RowData &X, int64_t iZ, RowData &Z, int64_t &iV, RowData &V) {
+        if (iZ >= 0) load_slots<T, kDense>(P, vals, Z, lane);
+        iV = iZ >= 0 ? row_of(P, t + 3 * W, bad) : -1;
+        if (iV >= 0) load_meta<kDense>(P, iV, V);
+        process_row<T, kDense>(P, vals, iX, X, lane);
         if (P.fence_each) {
             __threadfence();
             __syncwarp();
@@ -175,17 +174,23 @@ __global__ void __launch_bounds__(kUpdateBlock, 3) update_kernel(const UpdatePar
             const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
             if (now > deadline) {
                 if (lane == 0) atomicOr(P.status, 1);
-                return;
+                stop = true;
             }
         }
         t += W;
-        i_cur = i_n1;
-        cur = n1;
-        i_n1 = i_n2;
-        n1 = n2;
-        i_n2 = i_n3;
-        n2 = n3;
+    };
+#pragma unroll 1
+    while (true) {
+        if (iA < 0 || stop) break;
+        step(iA, rA, iC, rC, iD, rD);
+        if (iB < 0 || stop) break;
+        step(iB, rB, iD, rD, iA, rA);
+        if (iC < 0 || stop) break;
+        step(iC, rC, iA, rA, iB, rB);
+        if (iD < 0 || stop) break;
+        step(iD, rD, iB, rB, iC, rC);
     }
+    if (stop) return;
     if (bad && lane == 0) atomicOr(P.status, 2);
 }
 

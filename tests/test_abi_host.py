@@ -113,3 +113,23 @@ def test_valid_problem_without_gpu_reports_cuda_error(lib):
         pytest.skip("a GPU is present")
     s, err = create(*small_csr())
     assert s == asaga.ECUDA and err
+
+
+def test_validation_of_a_large_problem_reports_the_first_bad_row(lib):
+    """Validation runs on several host threads; the reported error is still the first one."""
+    g = np.random.default_rng(0)
+    n, d, k = 300_000, 5000, 4
+    col = np.sort(g.integers(0, d // k, (n, k)) + np.arange(k) * (d // k), axis=1).astype(np.int32)
+    row_ptr = np.arange(n + 1, dtype=np.int64) * k
+    vals = np.ones(n * k)
+    y = np.ones(n)
+    assert create(row_ptr, col.ravel(), vals, y, n=n, d=d)[0] != asaga.EINVAL
+    bad = col.copy()
+    bad[250_000, 1] = bad[250_000, 0]
+    bad[280_000, 2] = bad[280_000, 0]
+    s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
+    assert s == asaga.EINVAL and "row 250000" in err
+    bad2 = col.copy()
+    bad2[299_999, 3] = d
+    s, err = create(row_ptr, bad2.ravel(), vals, y, n=n, d=d)
+    assert s == asaga.EINVAL and str(299_999 * k + 3) in err
