@@ -234,6 +234,45 @@ const char *asaga_last_error(const asaga_ctx *ctx);
 
 const char *asaga_status_string(asaga_status s);
 
+/* Columns the scratch of asaga_recompute_abar_noalloc holds (4 MiB of float64). */
+#define ASAGA_NOALLOC_MAX_D 524288
+
+/*
+ * asaga_recompute_abar_noalloc -- abar = (1/n) sum_i alpha_i a_i in float64,
+ * like asaga_recompute_abar, for data the caller keeps in device memory, and
+ * without allocating any device memory.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate -- a process that must keep
+ * a fixed device-memory footprint reserved up front (where an allocation at
+ * run time can fail or stall), code embedded in a framework that owns all
+ * device memory through its own allocator, or a path where the device-wide
+ * synchronisation of cudaFree is not acceptable.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   n, d      rows and columns; n >= 1, 1 <= d <= ASAGA_NOALLOC_MAX_D.
+ *   row_ptr   device int64[n+1], col_idx device int32[nnz], values device
+ *             float32[nnz]: the CSR matrix with the invariants of
+ *             asaga_problem (not validated here; the caller guarantees them).
+ *   alpha     device float32[n], the scalar memories alpha_i.
+ *   abar      device float32[d]; on entry the running averages (used only for
+ *             the drift), on return the recomputed values rounded to float32.
+ *   drift     device float64[1] or NULL; receives max_v |abar_v(entry) - exact_v|.
+ *   stream    cudaStream_t to run on (NULL: the default stream).  The call
+ *             only enqueues work; results are ready when the stream is.
+ * Scratch: a fixed float64[ASAGA_NOALLOC_MAX_D] array (plus 1024 float64
+ * partials) in the library's device code.  A GPU holds it from the time that
+ * code is loaded on it until the process exits.  Every call shares it and
+ * leaves the last call's sums in it (each call zeroes it first), so calls
+ * that overlap on the GPU -- on different streams or from different host
+ * threads -- race and corrupt each other's results; order them.  The first
+ * call on a device looks the scratch address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * EINVAL: n < 1, d outside [1, ASAGA_NOALLOC_MAX_D], a NULL array; ECUDA: a
+ * CUDA call failed.  asaga_last_error(NULL) gives the reason.
+ */
+asaga_status asaga_recompute_abar_noalloc(int64_t n, int64_t d, const int64_t *row_ptr,
+                                          const int32_t *col_idx, const float *values,
+                                          const float *alpha, float *abar, double *drift,
+                                          void *stream);
+
 /* Frees the context and its device memory; NULL is a no-op. */
 void asaga_destroy(asaga_ctx *ctx);
 

@@ -114,6 +114,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_last_error.restype = ctypes.c_char_p
     L.asaga_status_string.argtypes = [i32]
     L.asaga_status_string.restype = ctypes.c_char_p
+    L.asaga_recompute_abar_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
+    L.asaga_recompute_abar_noalloc.restype = i32
     L.asaga_destroy.argtypes = [vp]
     L.asaga_destroy.restype = None
     for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_autotune", "asaga_objective", "asaga_full_grad",
@@ -238,6 +240,17 @@ def asaga_recompute_abar(ctx: int) -> float:
     drift = ctypes.c_double()
     _check(ctx, load().asaga_recompute_abar(ctx, ctypes.byref(drift)))
     return drift.value
+
+
+NOALLOC_MAX_D = 524288
+
+
+def asaga_recompute_abar_noalloc(n, d, row_ptr, col_idx, values, alpha, abar, drift=None, stream=None) -> None:
+    """Device-pointer (torch CUDA tensor) form of the allocation-free abar
+    recomputation; raises AsagaError on EINVAL / ECUDA."""
+    s = load().asaga_recompute_abar_noalloc(int(n), int(d), _ptr(row_ptr), _ptr(col_idx), _ptr(values),
+                                            _ptr(alpha), _ptr(abar), _ptr(drift), stream)
+    _check(None, s)
 
 
 def asaga_get_state(ctx: int):

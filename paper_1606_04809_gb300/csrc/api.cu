@@ -770,6 +770,10 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
 
 }  // namespace
 
+namespace asaga {
+void set_thread_error(const std::string &msg) { g_create_err = msg; }
+}  // namespace asaga
+
 extern "C" {
 
 void asaga_default_options(asaga_options *o) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace asaga {
 
 // Device element type of A's values.
@@ -60,6 +62,9 @@ constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
 constexpr int kEvalBlock = 256;
 constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
 constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in shared memory
+
+// api.cu: the text asaga_last_error(NULL) returns on this host thread.
+void set_thread_error(const std::string &msg);
 
 // update.cu
 cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
