@@ -147,7 +147,7 @@ typedef struct {
 typedef struct {
     int warps;           /* chosen number of concurrent solver warps            */
     double gamma;        /* chosen step size                                    */
-    double score;        /* decrease of ln |grad f|^2 per device second          */
+    double score;        /* ln(1e6) / device seconds of the winning trial        */
     int trials;          /* (warps, gamma) pairs tried                          */
     double seconds;      /* device time spent in the trials                      */
 } asaga_tune_result;
@@ -181,16 +181,18 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
 /* Picks the number of concurrent warps and the step size for asaga_run.
  * The overlap tau of asynchronous updates grows with the number of warps,
  * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)),
- * so this runs short trials -- trial_epochs epochs each (<= 0: 6) from
- * x = 0, alpha = 0 -- starting at the resident maximum of warps (at most
- * n/4) and halving down to 32, with steps gamma0 * 2^(-k/2) (gamma0 =
- * options.gamma or 1/(3L)).  For each warp count it keeps the largest step
- * under which the float64 |grad f|^2 decreases monotonically over the last
- * two trial epochs, scores it by the decrease of ln |grad f|^2 per device
- * second, and stops once the score has peaked.  The chosen step is 0.7x the
- * largest stable one (a margin for runs longer than a trial).  Leaves the
- * state at x = 0, alpha = 0, abar = 0 (sampler position 0) with the chosen
- * pair in use.  EINVAL in deterministic mode. */
+ * so the fastest schedule is found by measurement.  Each trial starts from
+ * x = 0, alpha = 0 and runs epochs with one (warps, gamma) pair until the
+ * float64 |grad f|^2 has shrunk by 1e-6 (or diverges, or reaches
+ * trial_epochs epochs (<= 0: 40), or is already 1.5x slower than the best
+ * trial).  Warp counts go from the resident maximum (at most n/4) down by
+ * halves to 32; for each, steps gamma0 * 2^(-k/2) (gamma0 = options.gamma or
+ * 1/(3L)) are tried from large to small until the time stops improving.
+ * The pair with the least update-kernel time wins; the step used is one
+ * notch (1/sqrt 2) below the winning one, a margin for run-to-run variation
+ * of asynchronous execution.  score = ln(1e6) / (winning time in seconds).
+ * Leaves the state at x = 0, alpha = 0, abar = 0 (sampler position 0) with
+ * the chosen pair in use.  EINVAL in deterministic mode. */
 asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);
 
 /* Deterministic replay: runs one update per entry of idx (row indices in

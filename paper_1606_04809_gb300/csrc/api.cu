@@ -651,12 +651,39 @@ asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, doub
     return ASAGA_OK;
 }
 
+// One trial of the autotuner: from x = 0, run epochs with (W, gamma) until
+// |grad f|^2 <= reduction * |grad f(0)|^2 (success), divergence, max_epochs,
+// or more update-kernel time than `give_up_ms`.  Returns the kernel time.
+asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, double reduction, int max_epochs,
+                        double give_up_ms, bool *success, double *t_ms, int *epochs, std::string *err) {
+    TRY(reset_state(c, err));
+    *success = false;
+    *t_ms = 0;
+    *epochs = 0;
+    double g_min = g0;
+    for (int e = 1; e <= max_epochs; ++e) {
+        double ms = 0, g = 0;
+        TRY(trial_epoch(c, W, gamma, &ms, &g, err));
+        *t_ms += ms;
+        *epochs = e;
+        if (!std::isfinite(g) || (e >= 3 && g > 4.0 * g_min)) return ASAGA_OK;  // diverging
+        g_min = std::min(g_min, g);
+        if (g <= reduction * g0) {
+            *success = true;
+            return ASAGA_OK;
+        }
+        if (*t_ms > give_up_ms) return ASAGA_OK;
+    }
+    return ASAGA_OK;
+}
+
 asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int E = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 6;
-    // warp counts, largest first: the resident maximum (bounded by n/4), then halvings down to 32
+    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 40;
+    const double reduction = 1e-6;  // trials race to shrink |grad f|^2 by this factor
+    // warp counts, largest first: the resident maximum (at most n/4), then halvings down to 32
     std::vector<int> cands;
     const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
     cands.push_back((int)cap);
@@ -664,10 +691,8 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     while (w * 2 < cap) w *= 2;
     for (; w >= 32; w /= 2)
         if (w < cap) cands.push_back((int)w);
-    // step scales: powers of 2^-1/2
-    std::vector<double> scales;
+    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2)
     for (int k = 0; k <= 12; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
-    const double kMargin = 0.7;  // the step used is 0.7x the largest one found stable in a trial
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -678,49 +703,43 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
     TRY(stream_sync(c, err));
     const double g0 = c->hout[2];
-    size_t first_scale = 0;
-    double best_scale = 0;
+    double best_ms = INFINITY;
+    size_t best_k = 0, first_k = 0;
     for (int W : cands) {
-        bool found = false;
-        for (size_t k = first_scale; k < scales.size(); ++k) {
-            const double gamma = c->gamma_base * scales[k];
-            TRY(reset_state(c, err));
-            double g[3] = {g0, g0, g0};
+        double w_best = INFINITY;
+        long w_k = -1;
+        for (size_t k = first_k; k < scales.size(); ++k) {
+            bool ok = false;
             double t_ms = 0;
-            bool ok = true;
-            for (int e = 1; e <= E; ++e) {
-                double ms = 0, g2 = g0;
-                TRY(trial_epoch(c, W, gamma, &ms, e >= E - 2 ? &g2 : nullptr, err));
-                t_ms += ms;
-                if (e >= E - 2) {
-                    g[e - (E - 2)] = g2;
-                    if (!std::isfinite(g2) || g2 > 1e6 * g0) {
-                        ok = false;
-                        break;
-                    }
-                }
-            }
+            int ep = 0;
+            const double give_up = std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY;
+            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep,
+                           err));
             ++r.trials;
             r.seconds += t_ms * 1e-3;
-            const bool stable = ok && g[2] <= g[1] && g[1] <= g[0] && g[2] < g0;
-            if (!stable) continue;
-            found = true;
-            const double score = std::log(g0 / g[2]) / (t_ms * 1e-3);
-            if (score > r.score) {
-                r.score = score;
-                r.warps = W;
-                best_scale = scales[k];
+            if (ok && t_ms < w_best) {
+                w_best = t_ms;
+                w_k = (long)k;
+            } else if (w_k >= 0) {
+                break;  // smaller steps only get slower from here
             }
-            // halving the warps roughly halves the overlap: start one notch above next time
-            first_scale = k >= 2 ? k - 2 : 0;
-            break;
         }
-        if (found && r.score > 0 && r.warps != W) {
-            // past the best warp count: stop once the score has clearly dropped
-            if (W < r.warps / 2) break;
+        if (w_k < 0) continue;  // nothing converged at this warp count: try fewer warps
+        if (w_best < best_ms) {
+            best_ms = w_best;
+            best_k = (size_t)w_k;
+            r.warps = W;
+        } else if (w_best > 1.5 * best_ms) {
+            break;  // past the best warp count
         }
+        // half the warps roughly halves the overlap: larger steps become stable
+        first_k = w_k >= 2 ? (size_t)w_k - 2 : 0;
     }
-    if (r.score > 0) r.gamma = c->gamma_base * best_scale * kMargin;
+    if (std::isfinite(best_ms)) {
+        // one notch below the fastest step: asynchronous runs vary from run to run
+        r.gamma = c->gamma_base * scales[best_k] * std::sqrt(0.5);
+        r.score = std::log(1.0 / reduction) / (best_ms * 1e-3);
+    }
     TRY(reset_state(c, err));
     if (r.score > 0) {
         c->warps = r.warps;
