@@ -98,6 +98,11 @@ typedef struct {
  *   column_stride        spacing of the per-column state in 16-byte units
  *                        (1 = packed; 8 = one 128-byte line per column, which
  *                        spreads atomics on very small d); 0 = automatic.
+ *   hot_target           reductions per epoch that one L2 line should take:
+ *                        a frequent column with c rows gets min(15,
+ *                        c/hot_target) replica slots, so that the atomic adds
+ *                        of many warps spread over several L2 lines (a read
+ *                        sums the slots; x and abar are unchanged); 0 = 65536.
  */
 typedef struct {
     asaga_loss loss;
@@ -112,6 +117,7 @@ typedef struct {
     double timeout_s;
     void *cuda_stream;
     int column_stride;
+    int64_t hot_target;
 } asaga_options;
 
 /* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and
@@ -141,6 +147,8 @@ typedef struct {
     int column_stride;   /* per-column state spacing in 16-byte units           */
     int64_t device_bytes;/* device memory held by the context                   */
     int64_t max_row_len; /* longest row                                          */
+    int n_hot;           /* frequent columns with their own hot id                */
+    int replica_slots;   /* replica slots spread over the hot columns             */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */
@@ -154,7 +162,8 @@ typedef struct {
 
 /* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
  * automatic warps, asynchronous, seed 0, 1 epoch per segment, no abar
- * recomputation, no timeout, own stream, automatic column stride. */
+ * recomputation, no timeout, own stream, automatic column stride,
+ * hot_target 65536. */
 void asaga_default_options(asaga_options *opt);
 
 /* Validates the problem, copies it to the device in options->storage_dtype,
@@ -235,6 +244,63 @@ asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
 const char *asaga_last_error(const asaga_ctx *ctx);
 
 const char *asaga_status_string(asaga_status s);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems (regularisation paths, cross-validation
+ * folds) solved together.  Each instance keeps its own data and state, as a
+ * context would; one persistent update launch per segment covers every
+ * unfinished instance (a block of 4 warps serves one instance, and each
+ * instance owns a fixed set of blocks), the float64 objectives of all
+ * instances come from one batched launch, and the segment's work (parameter
+ * upload, update launch, objective launches, download of the objectives) is
+ * captured once into a CUDA graph and replayed every segment.
+ */
+typedef struct asaga_batch asaga_batch;
+
+/* Creates `count` instances from problems[i] and options[i] (loss, lambda,
+ * gamma, seed per instance).  All instances share options[0].storage_dtype,
+ * the sparse or dense layout, options[0].epochs_per_segment and
+ * options[0].abar_recompute_every, and run on options[0].cuda_stream.  The
+ * initial schedule gives instance i warps in proportion to its nonzeros (a
+ * multiple of 4, at least 4, at most max(4, n_i/16)) within the warps that
+ * can be resident at once.  EINVAL as asaga_create, or for mixed dtypes or
+ * layouts, deterministic options, or count < 1. */
+asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_problem *problems,
+                                const asaga_options *options);
+
+/* Runs segments over all unfinished instances until each has
+ * (f_i - f_star[i])/|f_star[i]| <= target (then it stops receiving updates)
+ * or max_epochs epochs have run.  results[i] (may be NULL) holds instance
+ * i's epochs, updates, f_last and rel_subopt; its solver_seconds is the
+ * device time of the shared segments up to the one after which it stopped,
+ * i.e. its time to target inside the batch.  f_star may be NULL when
+ * target <= 0.  OK when every instance reached the target (or target <= 0),
+ * ENOTCONVERGED otherwise, EDIVERGED if an objective turned non-finite. */
+asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, const double *f_star,
+                             asaga_result *results);
+
+/* Per-instance step sizes from shared trials: the schedule is reset to the
+ * default, and every trial runs all instances at once for trial_epochs
+ * epochs (<= 0: 8) from x = 0 with gamma_i = s * gamma0_i, s on the ladder
+ * 2^(-k/2); each instance keeps the s under which its float64 |grad f_i|^2
+ * fell most (decreasing over the last two epochs), one notch lower as a
+ * margin.  Leaves every instance at x = 0.  results[i] may be NULL. */
+asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);
+
+/* Overrides the schedule: warps[i] (rounded up to a multiple of 4) and/or
+ * gamma[i]; either array may be NULL.  EINVAL if the warps cannot all be
+ * resident at once. */
+asaga_status asaga_batch_set_schedule(asaga_batch *b, const int *warps, const double *gamma);
+
+/* As asaga_get_state / asaga_get_info for instance i. */
+asaga_status asaga_batch_get_state(asaga_batch *b, int i, float *x, float *abar, float *alpha);
+asaga_status asaga_batch_get_info(asaga_batch *b, int i, asaga_info *info);
+
+/* f_i of every instance (float64, one batched launch); f holds count values. */
+asaga_status asaga_batch_objective(asaga_batch *b, double *f);
+
+const char *asaga_batch_last_error(const asaga_batch *b);
+void asaga_batch_destroy(asaga_batch *b);
 
 /* Columns the scratch of asaga_recompute_abar_noalloc holds (4 MiB of float64). */
 #define ASAGA_NOALLOC_MAX_D 524288

@@ -47,7 +47,7 @@ class asaga_options(ctypes.Structure):
                 ("storage_dtype", ctypes.c_int), ("max_warps", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("epochs_per_segment", ctypes.c_int),
                 ("abar_recompute_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int), ("hot_target", ctypes.c_int64)]
 
 
 class asaga_result(ctypes.Structure):
@@ -64,7 +64,7 @@ class asaga_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64), ("L", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("warps", ctypes.c_int),
                 ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
-                ("max_row_len", ctypes.c_int64)]
+                ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("replica_slots", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -118,6 +118,20 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_recompute_abar_noalloc.restype = i32
     L.asaga_destroy.argtypes = [vp]
     L.asaga_destroy.restype = None
+    L.asaga_batch_create.argtypes = [P(vp), i32, P(asaga_problem), P(asaga_options)]
+    L.asaga_batch_run.argtypes = [vp, dbl, dbl, vp, vp]
+    L.asaga_batch_autotune.argtypes = [vp, dbl, vp]
+    L.asaga_batch_set_schedule.argtypes = [vp, vp, vp]
+    L.asaga_batch_get_state.argtypes = [vp, i32, vp, vp, vp]
+    L.asaga_batch_get_info.argtypes = [vp, i32, P(asaga_info)]
+    L.asaga_batch_objective.argtypes = [vp, vp]
+    L.asaga_batch_last_error.argtypes = [vp]
+    L.asaga_batch_last_error.restype = ctypes.c_char_p
+    L.asaga_batch_destroy.argtypes = [vp]
+    L.asaga_batch_destroy.restype = None
+    for f in ("asaga_batch_create", "asaga_batch_run", "asaga_batch_autotune", "asaga_batch_set_schedule",
+              "asaga_batch_get_state", "asaga_batch_get_info", "asaga_batch_objective"):
+        getattr(L, f).restype = i32
     for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_autotune", "asaga_objective", "asaga_full_grad",
               "asaga_recompute_abar", "asaga_get_state", "asaga_set_state", "asaga_get_info"):
         getattr(L, f).restype = i32
@@ -304,6 +318,103 @@ class Context:
         if self.ctx:
             asaga_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------- batches
+
+def _bcheck(b, status: int):
+    if status != OK:
+        raise AsagaError(status, load().asaga_batch_last_error(b).decode())
+
+
+def asaga_batch_create(problems, options) -> int:
+    n = len(problems)
+    P = (asaga_problem * n)(*[p.struct for p in problems])
+    O = (asaga_options * n)(*options)
+    b = ctypes.c_void_p()
+    _bcheck(None, load().asaga_batch_create(ctypes.byref(b), n, P, O))
+    return b.value
+
+
+def asaga_batch_run(b: int, count: int, max_epochs: float, target: float = 0.0, f_star=None):
+    """Returns (status, [asaga_result] * count); raises on EINVAL / ENOMEM / ECUDA."""
+    res = (asaga_result * count)()
+    fs = None if f_star is None else np.ascontiguousarray(f_star, dtype=np.float64)
+    s = load().asaga_batch_run(b, float(max_epochs), float(target), _ptr(fs), ctypes.cast(res, ctypes.c_void_p))
+    if s in (EINVAL, ENOMEM, ECUDA):
+        raise AsagaError(s, load().asaga_batch_last_error(b).decode())
+    return s, list(res)
+
+
+def asaga_batch_autotune(b: int, count: int, trial_epochs: float = 0.0) -> list:
+    res = (asaga_tune_result * count)()
+    _bcheck(b, load().asaga_batch_autotune(b, float(trial_epochs), ctypes.cast(res, ctypes.c_void_p)))
+    return [r.as_dict() for r in res]
+
+
+def asaga_batch_set_schedule(b: int, warps=None, gamma=None) -> None:
+    w = None if warps is None else np.ascontiguousarray(warps, dtype=np.int32)
+    g = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
+    _bcheck(b, load().asaga_batch_set_schedule(b, _ptr(w), _ptr(g)))
+
+
+def asaga_batch_get_state(b: int, i: int, d: int, n: int):
+    x = np.empty(d, dtype=np.float32)
+    abar = np.empty(d, dtype=np.float32)
+    alpha = np.empty(n, dtype=np.float32)
+    _bcheck(b, load().asaga_batch_get_state(b, int(i), _ptr(x), _ptr(abar), _ptr(alpha)))
+    return x, abar, alpha
+
+
+def asaga_batch_get_info(b: int, i: int) -> dict:
+    info = asaga_info()
+    _bcheck(b, load().asaga_batch_get_info(b, int(i), ctypes.byref(info)))
+    return info.as_dict()
+
+
+def asaga_batch_objective(b: int, count: int) -> np.ndarray:
+    f = np.empty(count, dtype=np.float64)
+    _bcheck(b, load().asaga_batch_objective(b, _ptr(f)))
+    return f
+
+
+def asaga_batch_destroy(b) -> None:
+    if b:
+        load().asaga_batch_destroy(b)
+
+
+class Batch:
+    """Owning wrapper over a batch of generated problems."""
+
+    def __init__(self, problems, *, storage: str, values_dtype: str = "f64", per_instance=None, **options):
+        self.problems = problems
+        self.structs = [host_problem(p, values_dtype) for p in problems]
+        opts = []
+        for k, p in enumerate(problems):
+            o = dict(loss=p.loss, lam=p.lam, storage_dtype=storage, seed=k)
+            o.update(options)
+            if per_instance:
+                o.update(per_instance[k])
+            opts.append(asaga_default_options(**o))
+        self.b = asaga_batch_create(self.structs, opts)
+        self.count = len(problems)
+
+    def close(self):
+        if self.b:
+            asaga_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

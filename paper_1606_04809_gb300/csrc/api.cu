@@ -55,15 +55,44 @@ struct asaga_ctx {
     double *partial = nullptr;
     double *dout = nullptr;  // [0] f, [1..] small results
     int *status = nullptr;
-    int *hot_slot = nullptr;  // d: shared-memory slot of a frequent column or -1
-    int *hot_col = nullptr;   // n_hot: column of each slot
+    int *hot_col = nullptr;   // n_hot: column of each hot id
+    int *hot_rep = nullptr;   // n_hot: replica slots of each hot id (<= 15)
+    float2 *rep = nullptr;    // n_hot * kRepStride replica slots
     int n_hot = 0;
+    int n_rep = 0;            // replica slots in use
+    int64_t hot_target = 65536;
     int64_t *idx_buf = nullptr;
     int64_t idx_cap = 0;
     double *hout = nullptr;  // pinned mirror of dout
     int *hstatus = nullptr;  // pinned
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 
+    std::string err;
+};
+
+// Many independent problems solved together (see asaga_batch_create).
+struct asaga_batch {
+    int count = 0;
+    std::vector<asaga_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int vtype = kF32;
+    bool dense = false;
+    int epochs_per_segment = 1;
+    int abar_every = 0;
+    int resident_blocks = 1;
+    std::vector<int> warps;        // per instance, a multiple of 4 (one block = 4 warps)
+    std::vector<int> block_begin;  // first block of each instance
+    int grid = 0;
+    int eval_grid = 1;             // blocks per instance in the batched objective
+    UpdateParams *d_up = nullptr, *h_up = nullptr;
+    EvalParams *d_ev = nullptr;
+    int *d_block_begin = nullptr;
+    double *d_partial = nullptr, *d_f = nullptr, *h_f = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int64_t launches = 0;
     std::string err;
 };
 
@@ -172,7 +201,7 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
         return fail(err, ASAGA_EINVAL, "storage_dtype must be F32, BF16 or F16");
     if (dtype_size(p->values_dtype) == 0) return fail(err, ASAGA_EINVAL, "unknown values_dtype");
     if (o->epochs_per_segment < 0 || o->abar_recompute_every < 0 || o->max_warps < 0 ||
-        o->column_stride < 0 || !(o->timeout_s >= 0))
+        o->column_stride < 0 || o->hot_target < 0 || !(o->timeout_s >= 0))
         return fail(err, ASAGA_EINVAL, "negative option");
     if (!p->values || !p->labels) return fail(err, ASAGA_EINVAL, "values or labels is NULL");
     int64_t nnz = p->nnz;
@@ -281,8 +310,7 @@ EvalParams eval_params(const asaga_ctx *c) {
     e.stride = c->stride;
     e.loss = c->loss;
     e.lambda = c->lambda;
-    e.hot_slot = c->hot_slot;
-    e.hot_col = c->hot_col;
+    e.hot_col = c->dense ? nullptr : c->hot_col;
     e.n_hot = c->n_hot;
     return e;
 }
@@ -313,24 +341,53 @@ asaga_status stream_sync(asaga_ctx *c, std::string *err) {
     return ASAGA_OK;
 }
 
-// The most frequent columns (at most kMaxHot, each in at least n/4096 rows)
-// get a per-block shared-memory accumulator in the float64 A^T w scatters.
+// Hot columns: the most frequent ones (at most kMaxHot, each in at least
+// max(64, n/4096) rows) get a hot id h.  Their entries in the device copy of
+// col_idx become -1 - h; the float64 scatters accumulate them per block in
+// shared memory, and the update kernel spreads their reductions over
+// min(15, count/hot_target) extra replica slots.  Dense problems with
+// d <= kMaxHot make every column hot (h = column, col_idx absent).
 asaga_status select_hot_columns(asaga_ctx *c, const std::vector<int> &count, std::string *err) {
-    const int64_t floor_count = std::max<int64_t>(64, c->n / 4096);
     std::vector<int> cand;
-    for (int64_t v = 0; v < c->d; ++v)
-        if (count[v] >= floor_count) cand.push_back((int)v);
-    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return count[a] != count[b] ? count[a] > count[b] : a < b; });
-    if ((int)cand.size() > kMaxHot) cand.resize(kMaxHot);
+    if (c->dense) {
+        if (c->d > kMaxHot) return ASAGA_OK;
+        for (int64_t v = 0; v < c->d; ++v) cand.push_back((int)v);
+    } else {
+        const int64_t floor_count = std::max<int64_t>(64, c->n / 4096);
+        for (int64_t v = 0; v < c->d; ++v)
+            if (count[v] >= floor_count) cand.push_back((int)v);
+        std::sort(cand.begin(), cand.end(),
+                  [&](int a, int b) { return count[a] != count[b] ? count[a] > count[b] : a < b; });
+        if ((int)cand.size() > kMaxHot) cand.resize(kMaxHot);
+    }
     c->n_hot = (int)cand.size();
     if (c->n_hot == 0) return ASAGA_OK;
-    std::vector<int> slot(c->d, -1);
-    for (int s = 0; s < c->n_hot; ++s) slot[cand[s]] = s;
-    TRY(dev_alloc(&c->hot_slot, c->d, c, err, "alloc hot slots"));
+    std::vector<int> reps(c->n_hot);
+    c->n_rep = 0;
+    for (int h = 0; h < c->n_hot; ++h) {
+        const int64_t cnt = c->dense ? c->n : count[cand[h]];
+        reps[h] = (int)std::min<int64_t>(kRepStride - 1, cnt / std::max<int64_t>(1, c->hot_target));
+        c->n_rep += reps[h];
+    }
     TRY(dev_alloc(&c->hot_col, c->n_hot, c, err, "alloc hot columns"));
-    CK(cudaMemcpyAsync(c->hot_slot, slot.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy slots");
+    TRY(dev_alloc(&c->hot_rep, c->n_hot, c, err, "alloc hot replicas"));
+    TRY(dev_alloc(&c->rep, (size_t)c->n_hot * kRepStride, c, err, "alloc replica slots"));
+    CK(cudaMemsetAsync(c->rep, 0, (size_t)c->n_hot * kRepStride * sizeof(float2), c->stream), "memset replicas");
     CK(cudaMemcpyAsync(c->hot_col, cand.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
        "copy hot columns");
+    CK(cudaMemcpyAsync(c->hot_rep, reps.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+       "copy hot replicas");
+    if (!c->dense) {
+        std::vector<int> hot_id(c->d, -1);
+        for (int h = 0; h < c->n_hot; ++h) hot_id[cand[h]] = h;
+        int *d_hot_id = nullptr;
+        CK(cudaMallocAsync((void **)&d_hot_id, c->d * sizeof(int), c->stream), "alloc hot map");
+        CK(cudaMemcpyAsync(d_hot_id, hot_id.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream),
+           "copy hot map");
+        CK(launch_encode_hot(c->col_idx, c->nnz, d_hot_id, c->stream), "encode hot columns");
+        ++c->launches;
+        CK(cudaFreeAsync(d_hot_id, c->stream), "free hot map");
+    }
     return stream_sync(c, err);
 }
 
@@ -450,8 +507,9 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
         int mx = 0;
         for (int v : count_h) mx = v > mx ? v : mx;
         c->delta = (double)mx / (double)c->n;
-        TRY(select_hot_columns(c, count_h, err));
     }
+    c->hot_target = o->hot_target > 0 ? o->hot_target : 65536;
+    TRY(select_hot_columns(c, count_h, err));
 
     // concurrency: resident warps of the update kernel, bounded by n so that
     // the overlap stays far below n/10 (Theorem 2's condition)
@@ -481,8 +539,9 @@ void release(asaga_ctx *c) {
     cudaFree(c->dout);
     cudaFree(c->status);
     cudaFree(c->idx_buf);
-    cudaFree(c->hot_slot);
     cudaFree(c->hot_col);
+    cudaFree(c->hot_rep);
+    cudaFree(c->rep);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstatus) cudaFreeHost(c->hstatus);
     for (auto &ev : c->ev)
@@ -515,6 +574,9 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.deadline_ns = 0;
     u.status = c->status;
+    u.hot_col = c->n_hot > 0 ? c->hot_col : nullptr;
+    u.hot_rep = c->hot_rep;
+    u.rep = c->rep;
     return u;
 }
 
@@ -524,6 +586,11 @@ asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
     const int grid = (u.nwarps + wpb - 1) / wpb;
     CK(launch_update(u, c->vtype, c->dense, grid, block, c->stream), "update kernel");
     ++c->launches;
+    if (c->n_rep > 0) {
+        CK(launch_fold_replicas(c->state, c->stride, c->hot_col, c->hot_rep, c->rep, c->n_hot, c->dense, c->stream),
+           "fold replicas");
+        ++c->launches;
+    }
     return ASAGA_OK;
 }
 
@@ -762,8 +829,6 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
             CK(cudaStreamSynchronize(c->stream), "sync");
             if (c->idx_buf) {
                 cudaFree(c->idx_buf);
-    cudaFree(c->hot_slot);
-    cudaFree(c->hot_col);
                 c->device_bytes -= c->idx_cap * (int64_t)sizeof(int64_t);
                 c->idx_buf = nullptr;
                 c->idx_cap = 0;
@@ -784,6 +849,322 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
     CK(cudaMemcpyAsync(c->hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
     TRY(stream_sync(c, err));
     if (*c->hstatus & 2) return fail(err, ASAGA_EINVAL, "index out of range in device index array");
+    return ASAGA_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+void batch_release(asaga_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto *c : b->ctx) release(c);
+    cudaFree(b->d_up);
+    cudaFree(b->d_ev);
+    cudaFree(b->d_block_begin);
+    cudaFree(b->d_partial);
+    cudaFree(b->d_f);
+    if (b->h_up) cudaFreeHost(b->h_up);
+    if (b->h_f) cudaFreeHost(b->h_f);
+    for (auto &e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+// Lays the schedule out: instance i owns warps[i]/4 consecutive blocks.
+asaga_status batch_layout(asaga_batch *b, std::string *err) {
+    b->block_begin.assign(b->count, 0);
+    int g = 0;
+    for (int i = 0; i < b->count; ++i) {
+        b->block_begin[i] = g;
+        g += std::max(1, b->warps[i] / 4);
+        b->h_up[i].nwarps = std::max(1, b->warps[i] / 4) * 4;
+    }
+    b->grid = g;
+    CK(cudaMemcpyAsync(b->d_block_begin, b->block_begin.data(), b->count * sizeof(int), cudaMemcpyHostToDevice,
+                       b->stream), "copy schedule");
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return ASAGA_OK;
+}
+
+// Default schedule: warps spread over the instances in proportion to their
+// nonzeros, multiples of 4, at least 4, at most max(4, n_i/16) (which keeps
+// each instance's overlap far below n_i/10), within the resident maximum.
+asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
+    const int64_t budget = (int64_t)b->resident_blocks * 4;
+    double total = 0;
+    for (auto *c : b->ctx) total += (double)std::max<int64_t>(c->nnz, c->n);
+    b->warps.assign(b->count, 4);
+    int64_t used = 0;
+    for (int i = 0; i < b->count; ++i) {
+        const asaga_ctx *c = b->ctx[i];
+        const double share = (double)std::max<int64_t>(c->nnz, c->n) / total * (double)budget;
+        int64_t w = std::max<int64_t>(4, ((int64_t)share / 4) * 4);
+        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 16 / 4) * 4));
+        b->warps[i] = (int)w;
+        used += w;
+    }
+    while (used > budget) {  // trim the largest shares until the schedule fits
+        int imax = (int)(std::max_element(b->warps.begin(), b->warps.end()) - b->warps.begin());
+        if (b->warps[imax] <= 4) break;
+        b->warps[imax] -= 4;
+        used -= 4;
+    }
+    return batch_layout(b, err);
+}
+
+asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *problems,
+                               const asaga_options *options, std::string *err) {
+    if (count < 1) return fail(err, ASAGA_EINVAL, "count must be >= 1");
+    if (!problems || !options) return fail(err, ASAGA_EINVAL, "problems or options is NULL");
+    for (int i = 1; i < count; ++i) {
+        if (options[i].storage_dtype != options[0].storage_dtype)
+            return fail(err, ASAGA_EINVAL, "all instances must share storage_dtype");
+        if ((problems[i].dense != 0) != (problems[0].dense != 0))
+            return fail(err, ASAGA_EINVAL, "all instances must be sparse or all dense");
+    }
+    for (int i = 0; i < count; ++i)
+        if (options[i].deterministic) return fail(err, ASAGA_EINVAL, "batches run asynchronously");
+    b->count = count;
+    CK(cudaGetDevice(&b->device), "cudaGetDevice");
+    if (options[0].cuda_stream) {
+        b->stream = (cudaStream_t)options[0].cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+        b->own_stream = true;
+    }
+    for (auto &e : b->ev) CK(cudaEventCreate(&e), "cudaEventCreate");
+    for (int i = 0; i < count; ++i) {
+        asaga_options o = options[i];
+        o.cuda_stream = b->stream;
+        asaga_ctx *c = new (std::nothrow) asaga_ctx();
+        if (!c) return fail(err, ASAGA_ENOMEM, "host allocation failed");
+        std::string e;
+        asaga_status st = create_impl(c, &problems[i], &o, &e);
+        if (st != ASAGA_OK) {
+            release(c);
+            return fail(err, st, "instance " + std::to_string(i) + ": " + e);
+        }
+        b->ctx.push_back(c);
+    }
+    b->vtype = b->ctx[0]->vtype;
+    b->dense = b->ctx[0]->dense;
+    b->epochs_per_segment = std::max(1, options[0].epochs_per_segment);
+    b->abar_every = options[0].abar_recompute_every;
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, b->device), "cudaGetDeviceProperties");
+    b->resident_blocks = prop.multiProcessorCount * batch_update_max_blocks_per_sm(b->vtype, b->dense);
+    b->eval_grid = std::max(1, std::min(64, (prop.multiProcessorCount * 8 + count - 1) / count));
+    CK(cudaMallocHost((void **)&b->h_up, count * sizeof(UpdateParams)), "alloc pinned");
+    CK(cudaMallocHost((void **)&b->h_f, count * sizeof(double)), "alloc pinned");
+    TRY(dev_alloc(&b->d_up, count, b->ctx[0], err, "alloc params"));
+    TRY(dev_alloc(&b->d_ev, count, b->ctx[0], err, "alloc params"));
+    TRY(dev_alloc(&b->d_block_begin, count, b->ctx[0], err, "alloc schedule"));
+    TRY(dev_alloc(&b->d_partial, 2 * (size_t)count * b->eval_grid, b->ctx[0], err, "alloc partials"));
+    TRY(dev_alloc(&b->d_f, count, b->ctx[0], err, "alloc objectives"));
+    std::vector<EvalParams> ev(count);
+    for (int i = 0; i < count; ++i) {
+        b->h_up[i] = update_params(b->ctx[i]);
+        b->h_up[i].count = 0;
+        b->h_up[i].fence_each = 0;
+        ev[i] = eval_params(b->ctx[i]);
+    }
+    CK(cudaMemcpyAsync(b->d_ev, ev.data(), count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
+       "copy params");
+    TRY(batch_default_schedule(b, err));
+    return stream_sync(b->ctx[0], err);
+}
+
+// Enqueues one segment: parameters in, one update launch over all
+// instances, the batched objective, objectives out.
+asaga_status batch_enqueue_segment(asaga_batch *b, std::string *err) {
+    CK(cudaMemcpyAsync(b->d_up, b->h_up, b->count * sizeof(UpdateParams), cudaMemcpyHostToDevice, b->stream),
+       "copy params");
+    CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->vtype, b->dense, b->stream),
+       "batch update kernel");
+    for (auto *c : b->ctx)
+        if (c->n_rep > 0)
+            CK(launch_fold_replicas(c->state, c->stride, c->hot_col, c->hot_rep, c->rep, c->n_hot, c->dense,
+                                    b->stream), "fold replicas");
+    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->vtype, b->dense, b->d_partial, b->d_f, b->stream),
+       "batch objective");
+    CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
+    return ASAGA_OK;
+}
+
+// Runs one segment through the captured graph (captured on first use).
+asaga_status batch_segment(asaga_batch *b, float *ms, std::string *err) {
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        asaga_status st = batch_enqueue_segment(b, err);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != ASAGA_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(err, e, "end capture");
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(err, e, "graph instantiate");
+    }
+    CK(cudaEventRecord(b->ev[0], b->stream), "event");
+    CK(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+    CK(cudaEventRecord(b->ev[1], b->stream), "event");
+    b->launches += 3;
+    CK(cudaStreamSynchronize(b->stream), "stream synchronize");
+    cudaEventElapsedTime(ms, b->ev[0], b->ev[1]);
+    return ASAGA_OK;
+}
+
+asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, const double *f_star,
+                            asaga_result *results, std::string *err) {
+    if (!(max_epochs >= 0) || !std::isfinite(max_epochs)) return fail(err, ASAGA_EINVAL, "max_epochs must be >= 0");
+    if (target > 0 && !f_star) return fail(err, ASAGA_EINVAL, "f_star is needed with a target");
+    if (target > 0)
+        for (int i = 0; i < b->count; ++i)
+            if (!std::isfinite(f_star[i]) || f_star[i] == 0.0)
+                return fail(err, ASAGA_EINVAL, "f_star must be finite and nonzero");
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<asaga_result> r(b->count);
+    for (auto &x : r) {
+        std::memset(&x, 0, sizeof(x));
+        x.f_last = NAN;
+        x.rel_subopt = NAN;
+    }
+    std::vector<char> active(b->count, 1);
+    double elapsed_ms = 0, epochs = 0;
+    int64_t seg = 0;
+    int n_active = b->count;
+    const int64_t launches0 = b->launches;
+    while (epochs < max_epochs && n_active > 0) {
+        const double ep = std::min((double)b->epochs_per_segment, max_epochs - epochs);
+        for (int i = 0; i < b->count; ++i) {
+            asaga_ctx *c = b->ctx[i];
+            UpdateParams &u = b->h_up[i];
+            u.gamma = (float)c->gamma;
+            u.t_begin = (uint64_t)c->updates_done;
+            u.count = active[i] ? (int64_t)std::llround(ep * (double)c->n) : 0;
+        }
+        float ms = 0;
+        TRY(batch_segment(b, &ms, err));
+        elapsed_ms += ms;
+        epochs += ep;
+        ++seg;
+        for (int i = 0; i < b->count; ++i) {
+            if (!active[i]) continue;
+            asaga_ctx *c = b->ctx[i];
+            c->updates_done += b->h_up[i].count;
+            r[i].updates += b->h_up[i].count;
+            r[i].epochs += ep;
+            r[i].segments = seg;
+            r[i].f_last = b->h_f[i];
+            r[i].solver_seconds = elapsed_ms * 1e-3;  // device time of the shared segments
+            if (f_star) r[i].rel_subopt = (r[i].f_last - f_star[i]) / std::fabs(f_star[i]);
+            const bool diverged = !std::isfinite(r[i].f_last);
+            const bool reached = target > 0 && r[i].rel_subopt <= target;
+            if (diverged || reached) {
+                active[i] = 0;
+                --n_active;
+            }
+        }
+        if (b->abar_every > 0 && seg % b->abar_every == 0) {
+            for (int i = 0; i < b->count; ++i)
+                if (active[i]) TRY(enqueue_recompute(b->ctx[i], err));
+            TRY(stream_sync(b->ctx[0], err));
+        }
+    }
+    const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    asaga_status st = ASAGA_OK;
+    for (int i = 0; i < b->count; ++i) {
+        r[i].seconds = wall;
+        r[i].kernel_launches = b->launches - launches0;
+        if (!std::isfinite(r[i].f_last)) st = ASAGA_EDIVERGED;
+        else if (target > 0 && !(r[i].rel_subopt <= target) && st == ASAGA_OK) st = ASAGA_ENOTCONVERGED;
+    }
+    if (results) std::copy(r.begin(), r.end(), results);
+    if (st != ASAGA_OK) fail(err, st, st == ASAGA_EDIVERGED ? "an instance diverged" : "max_epochs reached before the target");
+    return st;
+}
+
+// Per-instance step sizes from shared trials: every trial runs all
+// instances at once with gamma_i = s * gamma0_i for one scale s of the
+// ladder 2^(-k/2); each instance keeps the scale under which its float64
+// |grad f_i|^2 fell fastest (monotonically over the trial's last two epochs),
+// one notch lower as a margin.
+asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    const int E = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 8;
+    TRY(batch_default_schedule(b, err));
+    std::vector<double> g0(b->count), best(b->count, -1.0), best_scale(b->count, 0.0);
+    auto grads = [&](std::vector<double> &g) -> asaga_status {
+        for (int i = 0; i < b->count; ++i) {
+            TRY(enqueue_grad(b->ctx[i], err));
+            CK(cudaMemcpyAsync(b->ctx[i]->hout + 2, b->ctx[i]->dout + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                               b->stream), "copy");
+        }
+        TRY(stream_sync(b->ctx[0], err));
+        for (int i = 0; i < b->count; ++i) g[i] = b->ctx[i]->hout[2];
+        return ASAGA_OK;
+    };
+    for (auto *c : b->ctx) TRY(reset_state(c, err));
+    TRY(grads(g0));
+    int trials = 0;
+    double seconds = 0;
+    for (int k = 0; k <= 8; ++k) {
+        const double scale = std::pow(2.0, -0.5 * k);
+        for (auto *c : b->ctx) TRY(reset_state(c, err));
+        std::vector<double> g1(b->count), g2(b->count), g3(b->count);
+        double t_ms = 0;
+        for (int e = 1; e <= E; ++e) {
+            for (int i = 0; i < b->count; ++i) {
+                asaga_ctx *c = b->ctx[i];
+                b->h_up[i].gamma = (float)(c->gamma_base * scale);
+                b->h_up[i].t_begin = (uint64_t)c->updates_done;
+                b->h_up[i].count = c->n;
+            }
+            float ms = 0;
+            TRY(batch_segment(b, &ms, err));
+            t_ms += ms;
+            for (auto *c : b->ctx) c->updates_done += c->n;
+            if (e == E - 2) TRY(grads(g1));
+            if (e == E - 1) TRY(grads(g2));
+            if (e == E) TRY(grads(g3));
+        }
+        ++trials;
+        seconds += t_ms * 1e-3;
+        bool any_better = false;
+        for (int i = 0; i < b->count; ++i) {
+            const bool stable = std::isfinite(g3[i]) && g3[i] <= g2[i] && g2[i] <= g1[i] && g3[i] < g0[i];
+            if (!stable) continue;
+            const double score = std::log(g0[i] / g3[i]);
+            if (score > best[i]) {
+                best[i] = score;
+                best_scale[i] = scale;
+                any_better = true;
+            }
+        }
+        if (!any_better && k >= 2) break;  // smaller steps help no instance any more
+    }
+    for (int i = 0; i < b->count; ++i) {
+        asaga_ctx *c = b->ctx[i];
+        if (best[i] > 0) c->gamma = c->gamma_base * best_scale[i] * std::sqrt(0.5);
+        c->warps = b->warps[i];
+        TRY(reset_state(c, err));
+        if (res) {
+            res[i].warps = b->warps[i];
+            res[i].gamma = c->gamma;
+            res[i].score = best[i] > 0 ? best[i] / (seconds / trials) : -1.0;
+            res[i].trials = trials;
+            res[i].seconds = seconds;
+        }
+    }
     return ASAGA_OK;
 }
 
@@ -810,6 +1191,7 @@ void asaga_default_options(asaga_options *o) {
     o->timeout_s = 0.0;
     o->cuda_stream = nullptr;
     o->column_stride = 0;
+    o->hot_target = 0;
 }
 
 asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {
@@ -926,6 +1308,8 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->column_stride = c->stride;
     info->device_bytes = c->device_bytes;
     info->max_row_len = c->max_row_len;
+    info->n_hot = c->n_hot;
+    info->replica_slots = c->n_rep;
     return ASAGA_OK;
 }
 
@@ -937,5 +1321,94 @@ const char *asaga_status_string(asaga_status s) {
 }
 
 void asaga_destroy(asaga_ctx *c) { release(c); }
+
+asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_problem *problems,
+                                const asaga_options *options) {
+    if (!out) {
+        g_create_err = "out is NULL";
+        return ASAGA_EINVAL;
+    }
+    *out = nullptr;
+    asaga_batch *b = new (std::nothrow) asaga_batch();
+    if (!b) {
+        g_create_err = "host allocation failed";
+        return ASAGA_ENOMEM;
+    }
+    std::string err;
+    asaga_status s = batch_create_impl(b, count, problems, options, &err);
+    if (s != ASAGA_OK) {
+        g_create_err = err;
+        batch_release(b);
+        return s;
+    }
+    *out = b;
+    return ASAGA_OK;
+}
+
+asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, const double *f_star,
+                             asaga_result *results) {
+    if (!b) return ASAGA_EINVAL;
+    return batch_run_impl(b, max_epochs, target, f_star, results, &b->err);
+}
+
+asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results) {
+    if (!b) return ASAGA_EINVAL;
+    return batch_autotune_impl(b, trial_epochs, results, &b->err);
+}
+
+asaga_status asaga_batch_set_schedule(asaga_batch *b, const int *warps, const double *gamma) {
+    if (!b) return ASAGA_EINVAL;
+    std::string *err = &b->err;
+    if (warps) {
+        int64_t total = 0;
+        for (int i = 0; i < b->count; ++i) {
+            if (warps[i] < 1) return fail(err, ASAGA_EINVAL, "warps must be >= 1");
+            total += (warps[i] + 3) / 4;
+        }
+        if (total > (int64_t)b->resident_blocks)
+            return fail(err, ASAGA_EINVAL, "schedule needs more warps than can be resident at once");
+        for (int i = 0; i < b->count; ++i) b->warps[i] = ((warps[i] + 3) / 4) * 4;
+        TRY(batch_layout(b, err));
+    }
+    if (gamma)
+        for (int i = 0; i < b->count; ++i) {
+            if (!(gamma[i] > 0) || !std::isfinite(gamma[i])) return fail(err, ASAGA_EINVAL, "gamma must be > 0");
+            b->ctx[i]->gamma = gamma[i];
+        }
+    return ASAGA_OK;
+}
+
+asaga_status asaga_batch_get_state(asaga_batch *b, int i, float *x, float *abar, float *alpha) {
+    if (!b) return ASAGA_EINVAL;
+    if (i < 0 || i >= b->count) return fail(&b->err, ASAGA_EINVAL, "instance out of range");
+    asaga_status s = asaga_get_state(b->ctx[i], x, abar, alpha);
+    if (s != ASAGA_OK) b->err = b->ctx[i]->err;
+    return s;
+}
+
+asaga_status asaga_batch_get_info(asaga_batch *b, int i, asaga_info *info) {
+    if (!b) return ASAGA_EINVAL;
+    if (i < 0 || i >= b->count) return fail(&b->err, ASAGA_EINVAL, "instance out of range");
+    asaga_status s = asaga_get_info(b->ctx[i], info);
+    if (s == ASAGA_OK) info->warps = b->warps[i];
+    return s;
+}
+
+asaga_status asaga_batch_objective(asaga_batch *b, double *f) {
+    if (!b || !f) return ASAGA_EINVAL;
+    std::string *err = &b->err;
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->vtype, b->dense, b->d_partial, b->d_f, b->stream),
+       "batch objective");
+    CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
+    CK(cudaStreamSynchronize(b->stream), "sync");
+    std::copy(b->h_f, b->h_f + b->count, f);
+    return ASAGA_OK;
+}
+
+const char *asaga_batch_last_error(const asaga_batch *b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+void asaga_batch_destroy(asaga_batch *b) { batch_release(b); }
+
 
 }  // extern "C"

@@ -17,6 +17,14 @@ enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3 };
 // (x_v, abar_v) by one vector atomic.  Columns are spaced `stride` float4s
 // apart.
 //   .x = x_v, .y = abar_v, .z = D_v, .w = unused (0)
+//
+// Frequent ("hot") columns: the device copy of col_idx stores an entry of
+// hot column hot_col[h] as -1 - h.  Hot column h may have hot_rep[h] <= 15
+// replica slots rep[h * kRepStride + r] = {x part, abar part}: an update
+// adds to one slot (or to the main state), a read sums the main state and
+// all slots, and a fold after every update launch moves the slots back into
+// the main state.  Dense problems mark every column hot (h = column).
+constexpr int kRepStride = 16;
 
 // Launch parameters of the asynchronous update kernel (one update = one
 // sampled row, Algorithm 2).
@@ -39,6 +47,9 @@ struct UpdateParams {
     int fence_each;           // 1: fence after every update (single-warp order)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     int *status;              // bit 0: timed out, bit 1: bad index
+    const int *hot_col;       // n_hot: column of hot id h (nullptr if none)
+    const int *hot_rep;       // n_hot: replica slots of hot id h
+    float2 *rep;              // n_hot * kRepStride replica slots
 };
 
 // Float64 evaluation parameters (objective, gradient, abar recomputation).
@@ -53,15 +64,15 @@ struct EvalParams {
     int stride;
     int loss;
     double lambda;
-    const int *hot_slot;      // d entries: shared-memory slot of a frequent column, -1 otherwise (may be nullptr)
-    const int *hot_col;       // n_hot entries: column of each slot
+    const int *hot_col;       // n_hot entries: column of hot id h (sparse; nullptr if none)
     int n_hot;
 };
 
 constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
+constexpr int kBatchBlock = 128;   // threads per block of the batched update kernel (4 warps)
 constexpr int kEvalBlock = 256;
 constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
-constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in shared memory
+constexpr int kMaxHot = 2048;      // most frequent columns (hot ids)
 
 // api.cu: the text asaga_last_error(NULL) returns on this host thread.
 void set_thread_error(const std::string &msg);
@@ -70,6 +81,11 @@ void set_thread_error(const std::string &msg);
 cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
                           cudaStream_t s);
 int update_max_blocks_per_sm(int vtype, bool dense);
+// params[count] and block_begin[count] in device memory; instance i owns blocks
+// [block_begin[i], block_begin[i+1]) (the last one up to grid).
+cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int vtype,
+                                bool dense, cudaStream_t s);
+int batch_update_max_blocks_per_sm(int vtype, bool dense);
 
 // eval.cu
 // partial[0..grid) <- per-block sums of phi_i(a_i.x); partial[grid..2grid) <- sums of x_v^2.
@@ -78,6 +94,10 @@ cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, in
 // out[0] <- (sum partial[0..grid))/n + lambda/2 (sum partial[grid..2grid)).
 cudaError_t launch_objective_finish(const double *partial, int grid, double inv_n, double lambda,
                                     double *out, cudaStream_t s);
+// Objectives of `count` instances in one launch of grid x count blocks:
+// partial holds 2 * grid * count doubles; f_out[i] receives instance i's f.
+cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int vtype, bool dense,
+                                   double *partial, double *f_out, cudaStream_t s);
 // acc[v] += sum_i w_i a_iv with w_i = phi'_i(a_i.x)/n (mode 0) or alpha_i/n (mode 1).
 cudaError_t launch_scatter_rows(const EvalParams &p, int vtype, bool dense, int mode, int grid,
                                 double *acc, cudaStream_t s);
@@ -88,6 +108,12 @@ cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double
 // out[0] <- sum (mode 0) or max (mode 1) of partial[0..grid).
 cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out,
                                    cudaStream_t s);
+
+// Adds every replica slot into the main state and clears it (after each update launch).
+cudaError_t launch_fold_replicas(float4 *state, int stride, const int *hot_col, const int *hot_rep, float2 *rep,
+                                 int n_hot, bool dense, cudaStream_t s);
+// col_idx[k] <- -1 - hot_id[col_idx[k]] where hot_id >= 0.
+cudaError_t launch_encode_hot(int32_t *col_idx, int64_t nnz, const int *hot_id, cudaStream_t s);
 
 // prep (eval.cu)
 cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s);

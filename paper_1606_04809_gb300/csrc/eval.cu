@@ -17,8 +17,8 @@
 // results go to a partial array reduced by one block in a fixed order, so
 // objective values are bitwise reproducible.  Column scatters (A^T w) use
 // float64 atomics at L2; dense problems with few columns, and the most
-// frequent columns of sparse ones, first accumulate per block in shared
-// memory.
+// frequent columns of sparse ones (whose col_idx entries carry their hot id
+// as -1 - id), first accumulate per block in shared memory.
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -54,7 +54,8 @@ __device__ __forceinline__ double row_dot_thread(const EvalParams &P, const T *v
     FF acc;
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
-        const int c = dense ? k : __ldg(P.col_idx + start + k);
+        int c = dense ? k : __ldg(P.col_idx + start + k);
+        if (c < 0) c = __ldg(P.hot_col + (-1 - c));  // a hot column's entry
         ff_add_product(acc, to_f32(vals[start + k]), ld_state_ro(P.state + (int64_t)c * P.stride).x);
     }
     return ff_value(acc);
@@ -112,6 +113,53 @@ __global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalPa
     }
 }
 
+// The objective of many instances in one launch: blockIdx.y = instance,
+// blockIdx.x = one of gridDim.x blocks over that instance's rows.
+template <typename T, bool kDense>
+__global__ void __launch_bounds__(kEvalBlock) batch_objective_rows_kernel(const EvalParams *__restrict__ params,
+                                                                          double *partial) {
+    __shared__ EvalParams sp;
+    if (threadIdx.x == 0) sp = params[blockIdx.y];
+    __syncthreads();
+    const T *vals = static_cast<const T *>(sp.values);
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sp.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t start;
+        int len;
+        row_range<T, kDense>(sp, i, start, len);
+        acc += phi_f64(sp.loss, row_dot_thread<T>(sp, vals, start, len, kDense), sp.labels[i]);
+    }
+    double xx = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sp.d; v += (int64_t)gridDim.x * blockDim.x) {
+        const double xv = ld_state_ro(sp.state + v * sp.stride).x;
+        xx += xv * xv;
+    }
+    const double s1 = block_reduce(acc, false);
+    const double s2 = block_reduce(xx, false);
+    if (threadIdx.x == 0) {
+        double *p = partial + 2 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+        p[0] = s1;
+        p[1] = s2;
+    }
+}
+
+// f_out[i] <- (sum of instance i's row partials)/n_i + lambda_i/2 (sum of its x partials); one block per instance.
+__global__ void batch_objective_finish_kernel(const EvalParams *__restrict__ params, const double *partial, int grid,
+                                              double *f_out) {
+    const double *p = partial + 2 * (int64_t)blockIdx.x * grid;
+    double a = 0.0, b = 0.0;
+    for (int j = threadIdx.x; j < grid; j += blockDim.x) {
+        a += p[2 * j];
+        b += p[2 * j + 1];
+    }
+    const double sa = block_reduce(a, false);
+    const double sb = block_reduce(b, false);
+    if (threadIdx.x == 0) {
+        const EvalParams &e = params[blockIdx.x];
+        f_out[blockIdx.x] = sa / (double)e.n + 0.5 * e.lambda * sb;
+    }
+}
+
 __global__ void objective_finish_kernel(const double *partial, int grid, double inv_n, double lambda,
                                         double *out) {
     double a = 0.0, b = 0.0;
@@ -152,13 +200,16 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
         }
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
-            const int c = kDense ? k : __ldg(P.col_idx + start + k);
+            int c = kDense ? k : __ldg(P.col_idx + start + k);
             const double contrib = w * (double)to_f32(vals[start + k]);
-            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);
-            if (slot >= 0)
+            // dense: every column has a slot; sparse: hot entries carry their slot (hot id)
+            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 && c < 0 ? -1 - c : -1);
+            if (slot >= 0) {
                 atomicAdd(sacc + slot, contrib);
-            else
+            } else {
+                if (c < 0) c = __ldg(P.hot_col + (-1 - c));
                 atomicAdd(acc + c, contrib);
+            }
         }
     }
     if (kSlotsMode) {
@@ -285,6 +336,25 @@ cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, in
     return cudaGetLastError();
 }
 
+template <typename T, bool kDense>
+static void batch_objective_t(const EvalParams *params, int count, int grid, double *partial, cudaStream_t s) {
+    batch_objective_rows_kernel<T, kDense><<<dim3(grid, count), kEvalBlock, 0, s>>>(params, partial);
+}
+
+cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int vtype, bool dense,
+                                   double *partial, double *f_out, cudaStream_t s) {
+    switch (vtype) {
+    case kF32: dense ? batch_objective_t<float, true>(params, count, grid, partial, s) : batch_objective_t<float, false>(params, count, grid, partial, s); break;
+    case kBF16: dense ? batch_objective_t<__nv_bfloat16, true>(params, count, grid, partial, s) : batch_objective_t<__nv_bfloat16, false>(params, count, grid, partial, s); break;
+    case kF16: dense ? batch_objective_t<__half, true>(params, count, grid, partial, s) : batch_objective_t<__half, false>(params, count, grid, partial, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    batch_objective_finish_kernel<<<count, 256, 0, s>>>(params, partial, grid, f_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_objective_finish(const double *partial, int grid, double inv_n, double lambda, double *out,
                                     cudaStream_t s) {
     objective_finish_kernel<<<1, 256, 0, s>>>(partial, grid, inv_n, lambda, out);
@@ -295,7 +365,7 @@ template <typename T, bool kDense>
 static cudaError_t scatter_t(const EvalParams &p, int mode, int grid, double *acc, cudaStream_t s) {
     if (kDense && p.d <= kSmemCols) {
         scatter_rows_kernel<T, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
-    } else if (!kDense && p.n_hot > 0 && p.hot_slot) {
+    } else if (!kDense && p.n_hot > 0 && p.hot_col) {
         scatter_rows_kernel<T, kDense, 2><<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, mode, acc);
     } else {
         scatter_rows_kernel<T, kDense, 0><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);

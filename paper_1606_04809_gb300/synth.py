@@ -339,3 +339,25 @@ def url_like(seed: int = 31, n: int = 2_400_000, d: int = 3_200_000, storage: st
 def covtype_like(seed: int = 41, n: int = 581_000, d: int = 54, storage: str = "f16") -> Problem:
     """Covtype-shaped ridge: n=581000, d=54 dense, standardised N(0,1), fp16, lam=1e-3."""
     return dense_ridge(n, d, storage=storage, lam=1e-3, seed=seed, name=f"covtypelike_n{n}_d{d}_{storage}")
+
+
+def logistic_batch(count: int = 256, seed: int = 51, n_range=(10_000, 200_000), d_range=(1_000, 50_000),
+                   density_range=(0.005, 0.02), lam_range=(1e-6, 1e-2), storage: str = "bf16") -> list:
+    """Independent l2-logistic instances of uneven shape, as in a
+    regularisation path: n and d uniform in their ranges, density uniform
+    (rows of 1 + Poisson(density*d - 1) entries), Zipf(1.1) columns, |N(0,1)|
+    values row-normalised, lambda on a log grid over lam_range (instance k
+    gets the k-th grid point), values on the storage grid."""
+    g = _rng(seed, 0)
+    ns = g.integers(n_range[0], n_range[1] + 1, count)
+    ds = g.integers(d_range[0], d_range[1] + 1, count)
+    dens = g.uniform(density_range[0], density_range[1], count)
+    lams = np.logspace(math.log10(lam_range[0]), math.log10(lam_range[1]), count)
+    out = []
+    for k in range(count):
+        n, d = int(ns[k]), int(ds[k])
+        kmean = max(1.0, float(dens[k]) * d)
+        out.append(sparse_logistic(n, d, k_mean=kmean, k_min=1, k_max=max(1, min(d, int(4 * kmean) + 4)),
+                                   zipf_s=1.1, values="abs_normal", storage=storage, lam=float(lams[k]),
+                                   seed=seed * 1000 + k, name=f"batch{seed}_{k}_n{n}_d{d}_{storage}"))
+    return out
