@@ -53,6 +53,13 @@ WORKLOADS = {
 }
 ABAR_EVERY = 5
 TARGET = 1e-6
+# 256 independent l2-logistic instances (a regularisation path): BASELINE's batch configuration with n and d
+# scaled by 1/10 so that the seeded CPU generator and the float64 certificates stay within minutes
+BATCH = dict(count=256, seed=51, n_range=(1_000, 20_000), d_range=(100, 5_000), density_range=(0.005, 0.02),
+             lam_range=(1e-6, 1e-2), storage="bf16")
+BATCH_DESC = ("256 l2-logistic instances: n~U[1000,20000], d~U[100,5000], density~U[0.5%,2%], Zipf(1.1) columns, "
+              "|N(0,1)| row-normalised, lambda on a log grid 1e-6..1e-2, bf16 values, fp32 state "
+              "(n and d scaled 1/10 from the specified batch)")
 
 
 def parse():
@@ -61,7 +68,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rcv1like", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rcv1like", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--single-sample", type=int, default=32,
+                    help="batch workload: instances also solved one at a time in fp32 for comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
@@ -228,8 +237,111 @@ def run_reference(args, p, wl):
 # ---------------------------------------------------------------- our arm
 
 
+def run_batch(args):
+    """Batched bf16 solve of many instances vs the same instances solved one at a time in fp32."""
+    import torch
+    from paper_1606_04809_gb300 import asaga
+    from paper_1606_04809_gb300 import build as lib_build
+    from paper_1606_04809_gb300 import sharding
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib_build.build()
+    asaga.load()
+    ps_all = synth.logistic_batch(**BATCH)
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "fstar_batch256.json")))
+    fs_all = np.array([g["fstar"] for g in gold["instances"]])
+    for p, g in zip(ps_all, gold["instances"]):
+        if p.fingerprint()["structure_sha256"] != g["fingerprint"]["structure_sha256"]:
+            raise SystemExit("regenerated batch differs from the one f* was computed for")
+    mine = sharding.rank_instances([sharding.instance_cost(p) for p in ps_all], world, rank)
+    ps = [ps_all[i] for i in mine]
+    fs = fs_all[mine]
+    stream = torch.cuda.current_stream()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    b = asaga.Batch(ps, storage="bf16", values_dtype="bf16", epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
+                    cuda_stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    tune = asaga.asaga_batch_autotune(b.b, b.count)
+    tune_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        asaga.asaga_batch_run(b.b, b.count, 1)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        st, res = asaga.asaga_batch_run(b.b, b.count, 1)
+        launches += res[0].kernel_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    b.close()
+    # time to 1e-6 for every instance of the batch
+    b = asaga.Batch(ps, storage="bf16", values_dtype="bf16", epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
+                    cuda_stream=stream.cuda_stream)
+    asaga.asaga_batch_set_schedule(b.b, warps=[t["warps"] for t in tune], gamma=[t["gamma"] for t in tune])
+    t0 = time.perf_counter()
+    st, res = asaga.asaga_batch_run(b.b, b.count, 5000, TARGET, fs)
+    batch_wall = time.perf_counter() - t0
+    batch_dev = max(r.solver_seconds for r in res)
+    b.close()
+    ttt = {"status": asaga.STATUS_NAMES[st], "seconds_device": max_over_ranks(batch_dev), "seconds_wall": batch_wall,
+           "max_epochs": max(r.epochs for r in res), "mean_epochs": float(np.mean([r.epochs for r in res])),
+           "worst_rel_subopt": float(max(r.rel_subopt for r in res))}
+    # the same instances one launch at a time, fp32 (a sample, every k-th instance)
+    single = None
+    if args.single_sample > 0 and rank == 0:
+        step = max(1, len(ps) // args.single_sample)
+        sample = list(range(0, len(ps), step))[: args.single_sample]
+        tot_dev = tot_wall = tot_tune = 0.0
+        statuses = []
+        for i in sample:
+            with asaga.Context(ps[i], storage="f32", seed=i, abar_recompute_every=ABAR_EVERY,
+                               cuda_stream=stream.cuda_stream) as c:
+                t0 = time.perf_counter()
+                asaga.asaga_autotune(c.ctx, 20)
+                tot_tune += time.perf_counter() - t0
+                s1, r1 = asaga.asaga_run(c.ctx, 5000, TARGET, fs[i])
+                statuses.append(asaga.STATUS_NAMES[s1])
+                tot_dev += r1.solver_seconds + r1.eval_seconds
+                tot_wall += r1.seconds
+        batch_sample = float(max(res[i].solver_seconds for i in sample))
+        single = {"instances": len(sample), "storage": "f32", "sum_seconds_device": tot_dev,
+                  "sum_seconds_wall": tot_wall, "autotune_wall_seconds": tot_tune,
+                  "all_ok": all(x == "ASAGA_OK" for x in statuses),
+                  "batch_seconds_for_same_instances": batch_sample,
+                  "speedup_batch_vs_single": tot_dev / batch_sample if batch_sample > 0 else None}
+    if rank == 0:
+        line = {"metric": "epochs/s", "value": world * args.steps / (ms * 1e-3), "unit": "epochs/s (whole batch)",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 values, f32 state",
+                "data": "synthetic", "config": {"workload": BATCH_DESC, "instances_per_rank": len(ps),
+                                                "nnz_total": int(sum(p.nnz for p in ps_all))},
+                "instance_epochs_per_s": world * args.steps * len(ps) / (ms * 1e-3),
+                "time_to_target": ttt, "autotune_wall_seconds": tune_s, "one_at_a_time_fp32": single,
+                "gpu_launches": launches}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.workload == "batch":
+        return run_batch(args)
     world, rank, local = dist_env()
     wl = WORKLOADS[args.workload]
     p = wl["make"]()

@@ -79,8 +79,11 @@ typedef struct {
  * Solver options; asaga_default_options() fills every field.
  *   loss                 the phi_i above.
  *   lambda               l2 weight, >= 0 (the paper uses 1/n, Sec. 4.2).
- *   gamma                step size; <= 0 picks 1/(3L), L = c max_i |a_i|^2 +
- *                        lambda with c = 1/4 (logistic) or 1 (squared).
+ *   gamma                step size; <= 0 picks 1/(3L), where L = max_i (c |a_i|^2
+ *                        + lambda max_{v in S_i} D_v), c = 1/4 (logistic) or 1
+ *                        (squared), is the smoothness constant of the component
+ *                        the sparse update samples (its l2 part is projected
+ *                        and reweighted by D_i, Sec. 4.2).
  *   storage_dtype        device type of A's values: F32, BF16 or F16 (the
  *                        iterate, memory and dot products are always F32).
  *   max_warps            concurrent solver warps ("cores"); 0 = automatic
@@ -98,11 +101,6 @@ typedef struct {
  *   column_stride        spacing of the per-column state in 16-byte units
  *                        (1 = packed; 8 = one 128-byte line per column, which
  *                        spreads atomics on very small d); 0 = automatic.
- *   hot_target           reductions per epoch that one L2 line should take:
- *                        a frequent column with c rows gets min(15,
- *                        c/hot_target) replica slots, so that the atomic adds
- *                        of many warps spread over several L2 lines (a read
- *                        sums the slots; x and abar are unchanged); 0 = 65536.
  */
 typedef struct {
     asaga_loss loss;
@@ -117,7 +115,6 @@ typedef struct {
     double timeout_s;
     void *cuda_stream;
     int column_stride;
-    int64_t hot_target;
 } asaga_options;
 
 /* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and
@@ -140,15 +137,15 @@ typedef struct {
 /* Static facts about a context. */
 typedef struct {
     int64_t n, d, nnz;
-    double L;            /* c max_i |a_i|^2 + lambda, on the stored values      */
+    double L;            /* max_i (c |a_i|^2 + lambda max_{v in S_i} D_v), stored values */
     double gamma;        /* step size in use                                    */
     double delta;        /* max_v |{i : v in S_i}| / n (Sec. 3.4, "Sparsity")   */
     int warps;           /* concurrent solver warps of asaga_run                */
     int column_stride;   /* per-column state spacing in 16-byte units           */
     int64_t device_bytes;/* device memory held by the context                   */
     int64_t max_row_len; /* longest row                                          */
-    int n_hot;           /* frequent columns with their own hot id                */
-    int replica_slots;   /* replica slots spread over the hot columns             */
+    int n_hot;           /* frequent columns accumulated in shared memory by the
+                            float64 scatters                                    */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */
@@ -162,8 +159,7 @@ typedef struct {
 
 /* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
  * automatic warps, asynchronous, seed 0, 1 epoch per segment, no abar
- * recomputation, no timeout, own stream, automatic column stride,
- * hot_target 65536. */
+ * recomputation, no timeout, own stream, automatic column stride. */
 void asaga_default_options(asaga_options *opt);
 
 /* Validates the problem, copies it to the device in options->storage_dtype,

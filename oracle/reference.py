@@ -114,12 +114,22 @@ def hessian(p, x: np.ndarray) -> np.ndarray:
 
 
 def lipschitz(p) -> float:
-    """L = c max_i |a_i|^2 + lambda, c = 1/4 for logistic, 1 for squared: the
-    smoothness constant of the f_i (Eq. finiteSum assumption)."""
+    """Smoothness constant of the components Sparse SAGA samples.
+
+    With the l2 term projected as in Sec. 4.2, the update of row i is the
+    gradient step of f_i(x) = phi_i(a_i.x) + lambda/2 sum_{v in S_i} D_v x_v^2
+    (their mean over i is f, since E[D_i] = I on touched coordinates), whose
+    Hessian is phi'' a_i a_i^T + lambda D_i with phi'' <= c (c = 1/4 logistic,
+    1 squared).  So L = max_i (c |a_i|^2 + lambda max_{v in S_i} D_v).  With
+    the paper's lambda = 1/n the second term is 1/|{j : v in S_j}| <= 1."""
     A = csr(p)
     r2 = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    D = reweighting(p)
+    rows = np.repeat(np.arange(p.n), np.diff(p.row_ptr))
+    dmax = np.zeros(p.n)
+    np.maximum.at(dmax, rows, D[p.col_idx])
     c = 0.25 if p.loss == "logistic" else 1.0
-    return float(c * r2.max() + p.lam)
+    return float(np.max(c * r2 + p.lam * dmax))
 
 
 def column_counts(p) -> np.ndarray:
@@ -275,6 +285,8 @@ def certified_fstar(p, index_stream, *, gamma: Optional[float] = None, rel_tol: 
             b = suboptimality_bound(p, st.x)
             if log:
                 log(f"epoch {ep}: f={f:.17g} bound={b:.3e}")
+            if not (np.isfinite(f) and np.isfinite(b)):
+                raise RuntimeError(f"serial Sparse SAGA diverged at epoch {ep}")
             if b <= rel_tol * abs(f):
                 return {"fstar": f, "bound": b, "epochs": ep, "x": st.x.copy()}
     raise RuntimeError("f* not certified within max_epochs")

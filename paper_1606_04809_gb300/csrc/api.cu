@@ -55,12 +55,9 @@ struct asaga_ctx {
     double *partial = nullptr;
     double *dout = nullptr;  // [0] f, [1..] small results
     int *status = nullptr;
-    int *hot_col = nullptr;   // n_hot: column of each hot id
-    int *hot_rep = nullptr;   // n_hot: replica slots of each hot id (<= 15)
-    float2 *rep = nullptr;    // n_hot * kRepStride replica slots
+    int *hot_slot = nullptr;  // d: shared-memory slot of a frequent column or -1
+    int *hot_col = nullptr;   // n_hot: column of each slot
     int n_hot = 0;
-    int n_rep = 0;            // replica slots in use
-    int64_t hot_target = 65536;
     int64_t *idx_buf = nullptr;
     int64_t idx_cap = 0;
     double *hout = nullptr;  // pinned mirror of dout
@@ -201,7 +198,7 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
         return fail(err, ASAGA_EINVAL, "storage_dtype must be F32, BF16 or F16");
     if (dtype_size(p->values_dtype) == 0) return fail(err, ASAGA_EINVAL, "unknown values_dtype");
     if (o->epochs_per_segment < 0 || o->abar_recompute_every < 0 || o->max_warps < 0 ||
-        o->column_stride < 0 || o->hot_target < 0 || !(o->timeout_s >= 0))
+        o->column_stride < 0 || !(o->timeout_s >= 0))
         return fail(err, ASAGA_EINVAL, "negative option");
     if (!p->values || !p->labels) return fail(err, ASAGA_EINVAL, "values or labels is NULL");
     int64_t nnz = p->nnz;
@@ -310,7 +307,8 @@ EvalParams eval_params(const asaga_ctx *c) {
     e.stride = c->stride;
     e.loss = c->loss;
     e.lambda = c->lambda;
-    e.hot_col = c->dense ? nullptr : c->hot_col;
+    e.hot_slot = c->hot_slot;
+    e.hot_col = c->hot_col;
     e.n_hot = c->n_hot;
     return e;
 }
@@ -341,53 +339,26 @@ asaga_status stream_sync(asaga_ctx *c, std::string *err) {
     return ASAGA_OK;
 }
 
-// Hot columns: the most frequent ones (at most kMaxHot, each in at least
-// max(64, n/4096) rows) get a hot id h.  Their entries in the device copy of
-// col_idx become -1 - h; the float64 scatters accumulate them per block in
-// shared memory, and the update kernel spreads their reductions over
-// min(15, count/hot_target) extra replica slots.  Dense problems with
-// d <= kMaxHot make every column hot (h = column, col_idx absent).
+// The most frequent columns (at most kMaxHot, each in at least
+// max(64, n/4096) rows) get a per-block shared-memory accumulator in the
+// float64 A^T w scatters, where their atomics would otherwise serialise at
+// one L2 line.
 asaga_status select_hot_columns(asaga_ctx *c, const std::vector<int> &count, std::string *err) {
+    const int64_t floor_count = std::max<int64_t>(64, c->n / 4096);
     std::vector<int> cand;
-    if (c->dense) {
-        if (c->d > kMaxHot) return ASAGA_OK;
-        for (int64_t v = 0; v < c->d; ++v) cand.push_back((int)v);
-    } else {
-        const int64_t floor_count = std::max<int64_t>(64, c->n / 4096);
-        for (int64_t v = 0; v < c->d; ++v)
-            if (count[v] >= floor_count) cand.push_back((int)v);
-        std::sort(cand.begin(), cand.end(),
-                  [&](int a, int b) { return count[a] != count[b] ? count[a] > count[b] : a < b; });
-        if ((int)cand.size() > kMaxHot) cand.resize(kMaxHot);
-    }
+    for (int64_t v = 0; v < c->d; ++v)
+        if (count[v] >= floor_count) cand.push_back((int)v);
+    std::sort(cand.begin(), cand.end(), [&](int a, int b) { return count[a] != count[b] ? count[a] > count[b] : a < b; });
+    if ((int)cand.size() > kMaxHot) cand.resize(kMaxHot);
     c->n_hot = (int)cand.size();
     if (c->n_hot == 0) return ASAGA_OK;
-    std::vector<int> reps(c->n_hot);
-    c->n_rep = 0;
-    for (int h = 0; h < c->n_hot; ++h) {
-        const int64_t cnt = c->dense ? c->n : count[cand[h]];
-        reps[h] = (int)std::min<int64_t>(kRepStride - 1, cnt / std::max<int64_t>(1, c->hot_target));
-        c->n_rep += reps[h];
-    }
+    std::vector<int> slot(c->d, -1);
+    for (int s = 0; s < c->n_hot; ++s) slot[cand[s]] = s;
+    TRY(dev_alloc(&c->hot_slot, c->d, c, err, "alloc hot slots"));
     TRY(dev_alloc(&c->hot_col, c->n_hot, c, err, "alloc hot columns"));
-    TRY(dev_alloc(&c->hot_rep, c->n_hot, c, err, "alloc hot replicas"));
-    TRY(dev_alloc(&c->rep, (size_t)c->n_hot * kRepStride, c, err, "alloc replica slots"));
-    CK(cudaMemsetAsync(c->rep, 0, (size_t)c->n_hot * kRepStride * sizeof(float2), c->stream), "memset replicas");
+    CK(cudaMemcpyAsync(c->hot_slot, slot.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy slots");
     CK(cudaMemcpyAsync(c->hot_col, cand.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
        "copy hot columns");
-    CK(cudaMemcpyAsync(c->hot_rep, reps.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
-       "copy hot replicas");
-    if (!c->dense) {
-        std::vector<int> hot_id(c->d, -1);
-        for (int h = 0; h < c->n_hot; ++h) hot_id[cand[h]] = h;
-        int *d_hot_id = nullptr;
-        CK(cudaMallocAsync((void **)&d_hot_id, c->d * sizeof(int), c->stream), "alloc hot map");
-        CK(cudaMemcpyAsync(d_hot_id, hot_id.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream),
-           "copy hot map");
-        CK(launch_encode_hot(c->col_idx, c->nnz, d_hot_id, c->stream), "encode hot columns");
-        ++c->launches;
-        CK(cudaFreeAsync(d_hot_id, c->stream), "free hot map");
-    }
     return stream_sync(c, err);
 }
 
@@ -492,14 +463,15 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
            "copy counts");
         CK(cudaFreeAsync(count, c->stream), "free counts");
     }
-    // L = c max_i |a_i|^2 + lambda on the stored values
-    const EvalParams e = eval_params(c);
-    CK(launch_max_row_norm2(e, c->vtype, c->dense, c->eval_grid, c->partial, c->dout, c->stream), "norm kernel");
-    c->launches += 2;
-    CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy norm");
-    TRY(stream_sync(c, err));
+    // L = max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) on the stored values
     const double cl = c->loss == ASAGA_LOSS_LOGISTIC ? 0.25 : 1.0;
-    c->L = cl * c->hout[0] + c->lambda;
+    const EvalParams e = eval_params(c);
+    CK(launch_max_row_smoothness(e, c->vtype, c->dense, cl, c->eval_grid, c->partial, c->dout, c->stream),
+       "smoothness kernel");
+    c->launches += 2;
+    CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy L");
+    TRY(stream_sync(c, err));
+    c->L = c->hout[0] > 0 ? c->hout[0] : (c->lambda > 0 ? c->lambda : 1.0);
     c->gamma = o->gamma > 0 ? o->gamma : (c->L > 0 ? 1.0 / (3.0 * c->L) : 1.0);
     if (c->dense) {
         c->delta = 1.0;
@@ -508,8 +480,7 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
         for (int v : count_h) mx = v > mx ? v : mx;
         c->delta = (double)mx / (double)c->n;
     }
-    c->hot_target = o->hot_target > 0 ? o->hot_target : 65536;
-    TRY(select_hot_columns(c, count_h, err));
+    if (!c->dense) TRY(select_hot_columns(c, count_h, err));
 
     // concurrency: resident warps of the update kernel, bounded by n so that
     // the overlap stays far below n/10 (Theorem 2's condition)
@@ -539,9 +510,8 @@ void release(asaga_ctx *c) {
     cudaFree(c->dout);
     cudaFree(c->status);
     cudaFree(c->idx_buf);
+    cudaFree(c->hot_slot);
     cudaFree(c->hot_col);
-    cudaFree(c->hot_rep);
-    cudaFree(c->rep);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstatus) cudaFreeHost(c->hstatus);
     for (auto &ev : c->ev)
@@ -574,9 +544,6 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.deadline_ns = 0;
     u.status = c->status;
-    u.hot_col = c->n_hot > 0 ? c->hot_col : nullptr;
-    u.hot_rep = c->hot_rep;
-    u.rep = c->rep;
     return u;
 }
 
@@ -586,11 +553,6 @@ asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
     const int grid = (u.nwarps + wpb - 1) / wpb;
     CK(launch_update(u, c->vtype, c->dense, grid, block, c->stream), "update kernel");
     ++c->launches;
-    if (c->n_rep > 0) {
-        CK(launch_fold_replicas(c->state, c->stride, c->hot_col, c->hot_rep, c->rep, c->n_hot, c->dense, c->stream),
-           "fold replicas");
-        ++c->launches;
-    }
     return ASAGA_OK;
 }
 
@@ -987,10 +949,6 @@ asaga_status batch_enqueue_segment(asaga_batch *b, std::string *err) {
        "copy params");
     CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->vtype, b->dense, b->stream),
        "batch update kernel");
-    for (auto *c : b->ctx)
-        if (c->n_rep > 0)
-            CK(launch_fold_replicas(c->state, c->stride, c->hot_col, c->hot_rep, c->rep, c->n_hot, c->dense,
-                                    b->stream), "fold replicas");
     CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->vtype, b->dense, b->d_partial, b->d_f, b->stream),
        "batch objective");
     CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
@@ -1191,7 +1149,6 @@ void asaga_default_options(asaga_options *o) {
     o->timeout_s = 0.0;
     o->cuda_stream = nullptr;
     o->column_stride = 0;
-    o->hot_target = 0;
 }
 
 asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {
@@ -1309,7 +1266,6 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->device_bytes = c->device_bytes;
     info->max_row_len = c->max_row_len;
     info->n_hot = c->n_hot;
-    info->replica_slots = c->n_rep;
     return ASAGA_OK;
 }
 

@@ -17,14 +17,7 @@ enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3 };
 // (x_v, abar_v) by one vector atomic.  Columns are spaced `stride` float4s
 // apart.
 //   .x = x_v, .y = abar_v, .z = D_v, .w = unused (0)
-//
-// Frequent ("hot") columns: the device copy of col_idx stores an entry of
-// hot column hot_col[h] as -1 - h.  Hot column h may have hot_rep[h] <= 15
-// replica slots rep[h * kRepStride + r] = {x part, abar part}: an update
-// adds to one slot (or to the main state), a read sums the main state and
-// all slots, and a fold after every update launch moves the slots back into
-// the main state.  Dense problems mark every column hot (h = column).
-constexpr int kRepStride = 16;
+
 
 // Launch parameters of the asynchronous update kernel (one update = one
 // sampled row, Algorithm 2).
@@ -47,9 +40,6 @@ struct UpdateParams {
     int fence_each;           // 1: fence after every update (single-warp order)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     int *status;              // bit 0: timed out, bit 1: bad index
-    const int *hot_col;       // n_hot: column of hot id h (nullptr if none)
-    const int *hot_rep;       // n_hot: replica slots of hot id h
-    float2 *rep;              // n_hot * kRepStride replica slots
 };
 
 // Float64 evaluation parameters (objective, gradient, abar recomputation).
@@ -64,7 +54,8 @@ struct EvalParams {
     int stride;
     int loss;
     double lambda;
-    const int *hot_col;       // n_hot entries: column of hot id h (sparse; nullptr if none)
+    const int *hot_slot;      // d entries: shared-memory slot of a frequent column, -1 otherwise (may be nullptr)
+    const int *hot_col;       // n_hot entries: column of each slot
     int n_hot;
 };
 
@@ -72,7 +63,7 @@ constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
 constexpr int kBatchBlock = 128;   // threads per block of the batched update kernel (4 warps)
 constexpr int kEvalBlock = 256;
 constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
-constexpr int kMaxHot = 2048;      // most frequent columns (hot ids)
+constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in shared memory
 
 // api.cu: the text asaga_last_error(NULL) returns on this host thread.
 void set_thread_error(const std::string &msg);
@@ -109,20 +100,15 @@ cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double
 cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out,
                                    cudaStream_t s);
 
-// Adds every replica slot into the main state and clears it (after each update launch).
-cudaError_t launch_fold_replicas(float4 *state, int stride, const int *hot_col, const int *hot_rep, float2 *rep,
-                                 int n_hot, bool dense, cudaStream_t s);
-// col_idx[k] <- -1 - hot_id[col_idx[k]] where hot_id >= 0.
-cudaError_t launch_encode_hot(int32_t *col_idx, int64_t nnz, const int *hot_id, cudaStream_t s);
-
 // prep (eval.cu)
 cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s);
 // state[v] <- {0, 0, D_v, 0}, D_v = n/count_v (0 if count_v = 0); count may be nullptr (dense: D = 1).
 cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n,
                               cudaStream_t s);
-// out[0] <- max_i sum_k a_ik^2 (float64) over the stored values.
-cudaError_t launch_max_row_norm2(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
-                                 double *out, cudaStream_t s);
+// out[0] <- max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) (float64) over the stored
+// values; needs D in state.z.
+cudaError_t launch_max_row_smoothness(const EvalParams &p, int vtype, bool dense, double c_loss, int grid,
+                                      double *partial, double *out, cudaStream_t s);
 // dst (vtype) <- src (src_dtype: 0 f64, 1 f32, 2 bf16, 3 f16), count elements.
 cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype, int64_t count,
                            cudaStream_t s);

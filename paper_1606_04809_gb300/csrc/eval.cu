@@ -4,7 +4,8 @@
 //   gradient       1/n A^T phi'(A x) + lambda x
 //   abar recompute abar = 1/n sum_i alpha_i a_i  (Sec. 2, definition of abar)
 //   set-up         column counts -> D_v = n / |{i : v in S_i}| (Sec. 2),
-//                  max_i |a_i|^2 for L, value conversion to the storage type.
+//                  L = max_i (c |a_i|^2 + lambda max_{v in S_i} D_v),
+//                  value conversion to the storage type.
 //
 // One thread evaluates one row (grid-stride over rows), so the float64
 // phi of 32 rows runs as one warp instruction.  Row sums a_i . x are
@@ -17,8 +18,8 @@
 // results go to a partial array reduced by one block in a fixed order, so
 // objective values are bitwise reproducible.  Column scatters (A^T w) use
 // float64 atomics at L2; dense problems with few columns, and the most
-// frequent columns of sparse ones (whose col_idx entries carry their hot id
-// as -1 - id), first accumulate per block in shared memory.
+// frequent columns of sparse ones, first accumulate per block in shared
+// memory.
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -54,8 +55,7 @@ __device__ __forceinline__ double row_dot_thread(const EvalParams &P, const T *v
     FF acc;
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
-        int c = dense ? k : __ldg(P.col_idx + start + k);
-        if (c < 0) c = __ldg(P.hot_col + (-1 - c));  // a hot column's entry
+        const int c = dense ? k : __ldg(P.col_idx + start + k);
         ff_add_product(acc, to_f32(vals[start + k]), ld_state_ro(P.state + (int64_t)c * P.stride).x);
     }
     return ff_value(acc);
@@ -200,16 +200,13 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
         }
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
-            int c = kDense ? k : __ldg(P.col_idx + start + k);
+            const int c = kDense ? k : __ldg(P.col_idx + start + k);
             const double contrib = w * (double)to_f32(vals[start + k]);
-            // dense: every column has a slot; sparse: hot entries carry their slot (hot id)
-            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 && c < 0 ? -1 - c : -1);
-            if (slot >= 0) {
+            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);
+            if (slot >= 0)
                 atomicAdd(sacc + slot, contrib);
-            } else {
-                if (c < 0) c = __ldg(P.hot_col + (-1 - c));
+            else
                 atomicAdd(acc + c, contrib);
-            }
         }
     }
     if (kSlotsMode) {
@@ -260,8 +257,12 @@ __global__ void init_state_kernel(float4 *state, int stride, int64_t d, const in
     }
 }
 
+// Per row: c |a_i|^2 + lambda max_{v in S_i} D_v (the smoothness constant of
+// the component the sparse update samples, with the projected l2 term);
+// partial[b] <- the block's maximum.
 template <typename T, bool kDense>
-__global__ void __launch_bounds__(kEvalBlock) row_norm2_kernel(const EvalParams P, double *partial) {
+__global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalParams P, double c_loss,
+                                                                    double *partial) {
     const T *vals = static_cast<const T *>(P.values);
     const int lane = threadIdx.x & 31;
     const int64_t wpb = blockDim.x >> 5;
@@ -272,12 +273,14 @@ __global__ void __launch_bounds__(kEvalBlock) row_norm2_kernel(const EvalParams 
         int64_t start;
         int len;
         row_range<T, kDense>(P, i, start, len);
-        double s = 0.0;
+        double s = 0.0, dmax = 0.0;
         for (int k = lane; k < len; k += 32) {
             const double a = (double)to_f32(vals[start + k]);
             s += a * a;
+            const int c = kDense ? k : P.col_idx[start + k];
+            dmax = fmax(dmax, (double)ld_state_ro(P.state + (int64_t)c * P.stride).z);
         }
-        best = fmax(best, warp_sum(s));
+        best = fmax(best, c_loss * warp_sum(s) + P.lambda * warp_max(dmax));
     }
     const double r = block_reduce(best, true);
     if (threadIdx.x == 0) partial[blockIdx.x] = r;
@@ -365,7 +368,7 @@ template <typename T, bool kDense>
 static cudaError_t scatter_t(const EvalParams &p, int mode, int grid, double *acc, cudaStream_t s) {
     if (kDense && p.d <= kSmemCols) {
         scatter_rows_kernel<T, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
-    } else if (!kDense && p.n_hot > 0 && p.hot_col) {
+    } else if (!kDense && p.n_hot > 0 && p.hot_slot) {
         scatter_rows_kernel<T, kDense, 2><<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, mode, acc);
     } else {
         scatter_rows_kernel<T, kDense, 0><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
@@ -405,16 +408,16 @@ cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *c
 }
 
 template <typename T, bool kDense>
-static void norm_t(const EvalParams &p, int grid, double *partial, cudaStream_t s) {
-    row_norm2_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, partial);
+static void smooth_t(const EvalParams &p, double c_loss, int grid, double *partial, cudaStream_t s) {
+    row_smoothness_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, c_loss, partial);
 }
 
-cudaError_t launch_max_row_norm2(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
-                                 double *out, cudaStream_t s) {
+cudaError_t launch_max_row_smoothness(const EvalParams &p, int vtype, bool dense, double c_loss, int grid,
+                                      double *partial, double *out, cudaStream_t s) {
     switch (vtype) {
-    case kF32: dense ? norm_t<float, true>(p, grid, partial, s) : norm_t<float, false>(p, grid, partial, s); break;
-    case kBF16: dense ? norm_t<__nv_bfloat16, true>(p, grid, partial, s) : norm_t<__nv_bfloat16, false>(p, grid, partial, s); break;
-    case kF16: dense ? norm_t<__half, true>(p, grid, partial, s) : norm_t<__half, false>(p, grid, partial, s); break;
+    case kF32: dense ? smooth_t<float, true>(p, c_loss, grid, partial, s) : smooth_t<float, false>(p, c_loss, grid, partial, s); break;
+    case kBF16: dense ? smooth_t<__nv_bfloat16, true>(p, c_loss, grid, partial, s) : smooth_t<__nv_bfloat16, false>(p, c_loss, grid, partial, s); break;
+    case kF16: dense ? smooth_t<__half, true>(p, c_loss, grid, partial, s) : smooth_t<__half, false>(p, c_loss, grid, partial, s); break;
     default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();

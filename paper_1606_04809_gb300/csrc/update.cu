@@ -88,75 +88,24 @@ __device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool
     return sample_row(P.seed, P.t_begin + (uint64_t)t, P.n);
 }
 
-// Entry k of a row: its main-state column and its hot id (-1 if cold).
-template <bool kDense>
-__device__ __forceinline__ void resolve(const UpdateParams &P, int c_enc, int k, int &col, int &hid) {
-    if (kDense) {
-        col = k;
-        hid = P.hot_col ? k : -1;
-    } else if (c_enc < 0) {
-        hid = -1 - c_enc;
-        col = __ldg(P.hot_col + hid);
-    } else {
-        col = c_enc;
-        hid = -1;
-    }
-}
-
-// x^ and abar of a column: the main state plus, for a hot column, its replica slots.
-__device__ __forceinline__ float4 read_column(const UpdateParams &P, int col, int hid) {
-    float4 v = ld_state(P.state + (int64_t)col * P.stride);
-    if (hid >= 0) {
-        const int R = __ldg(P.hot_rep + hid);
-        const float2 *rp = P.rep + hid * kRepStride;
-        for (int r = 0; r < R; ++r) {
-            const float2 q = __ldcg(rp + r);
-            v.x += q.x;
-            v.y += q.y;
-        }
-    }
-    return v;
-}
-
-// Adds (dx, dab) to the column: to the main state or, for a hot column, to
-// one of its slots chosen by the warp, so that the warps spread their
-// reductions over several L2 lines.
-__device__ __forceinline__ void add_column(const UpdateParams &P, int col, int hid, int warp, float dx, float dab) {
-    if (hid >= 0) {
-        const int R = __ldg(P.hot_rep + hid);
-        const int r = warp % (R + 1);
-        if (r > 0) {
-            float2 *q = P.rep + hid * kRepStride + (r - 1);
-            asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(q), "f"(dx), "f"(dab) : "memory");
-            return;
-        }
-    }
-    red_add_v2(P.state + (int64_t)col * P.stride, dx, dab);
-}
-
 template <typename T, bool kDense>
 __device__ __forceinline__ void process_row(const UpdateParams &P, const T *__restrict__ vals, int64_t i,
-                                            const RowData &r, int lane, int warp) {
-    int col[kSlots], hid[kSlots];
+                                            const RowData &r, int lane) {
+    const float4 *__restrict__ state = P.state;
+    const int64_t stride = P.stride;
     float4 s[kSlots];
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
-        col[q] = 0;
-        hid[q] = -1;
         s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane + 32 * q < r.len) {
-            resolve<kDense>(P, r.c[q], lane + 32 * q, col[q], hid[q]);
-            s[q] = read_column(P, col[q], hid[q]);
-        }
+        if (lane + 32 * q < r.len) s[q] = ld_state(state + r.c[q] * stride);
     }
     const float alpha_hat = __ldcg(P.alpha + i);
     float z = 0.f;
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) z = fmaf(r.a[q], s[q].x, z);
     for (int k = lane + 32 * kSlots; k < r.len; k += 32) {  // rest of a long row
-        int cc, hh;
-        resolve<kDense>(P, kDense ? 0 : ld_stream(P.col_idx + r.start + k), k, cc, hh);
-        z = fmaf(to_f32(ld_stream(vals + r.start + k)), read_column(P, cc, hh).x, z);
+        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
+        z = fmaf(to_f32(ld_stream(vals + r.start + k)), ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
     const float delta = phi_prime_f32(P.loss, z, r.label) - alpha_hat;  // same value in every lane
@@ -166,16 +115,15 @@ __device__ __forceinline__ void process_row(const UpdateParams &P, const T *__re
     for (int q = 0; q < kSlots; ++q) {
         if (lane + 32 * q < r.len) {
             const float dx = -gamma * fmaf(delta, r.a[q], s[q].z * fmaf(lambda, s[q].x, s[q].y));
-            add_column(P, col[q], hid[q], warp, dx, delta * r.a[q] * inv_n);
+            red_add_v2(P.state + r.c[q] * stride, dx, delta * r.a[q] * inv_n);
         }
     }
     for (int k = lane + 32 * kSlots; k < r.len; k += 32) {
-        int cc, hh;
-        resolve<kDense>(P, kDense ? 0 : ld_stream(P.col_idx + r.start + k), k, cc, hh);
+        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
         const float av = to_f32(ld_stream(vals + r.start + k));
-        const float4 sv = read_column(P, cc, hh);
+        const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
-        add_column(P, cc, hh, warp, dx, delta * av * inv_n);
+        red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
     }
     if (lane == 0) red_add_f32(P.alpha + i, delta);
 }
@@ -215,7 +163,7 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, int warp, in
         if (iZ >= 0) load_slots<T, kDense>(P, vals, Z, lane);
         iV = iZ >= 0 ? row_of(P, t + 3 * W, bad) : -1;
         if (iV >= 0) load_meta<kDense>(P, iV, V);
-        process_row<T, kDense>(P, vals, iX, X, lane, warp);
+        process_row<T, kDense>(P, vals, iX, X, lane);
         if (P.fence_each) {
             __threadfence();
             __syncwarp();
@@ -333,48 +281,6 @@ int batch_update_max_blocks_per_sm(int vtype, bool dense) {
     case kF16: return dense ? batch_occ<__half, true>() : batch_occ<__half, false>();
     default: return 1;
     }
-}
-
-__global__ void fold_replicas_kernel(float4 *state, int stride, const int *hot_col, const int *hot_rep,
-                                     float2 *rep, int n_hot) {
-    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n_hot; h += gridDim.x * blockDim.x) {
-        const int R = hot_rep[h];
-        if (R == 0) continue;
-        float sx = 0.f, sy = 0.f;
-        for (int r = 0; r < R; ++r) {
-            const float2 q = rep[h * kRepStride + r];
-            sx += q.x;
-            sy += q.y;
-            rep[h * kRepStride + r] = make_float2(0.f, 0.f);
-        }
-        float4 *m = state + (int64_t)hot_col[h] * stride;
-        m->x += sx;
-        m->y += sy;
-    }
-}
-
-cudaError_t launch_fold_replicas(float4 *state, int stride, const int *hot_col, const int *hot_rep, float2 *rep,
-                                 int n_hot, bool dense, cudaStream_t s) {
-    (void)dense;
-    if (n_hot <= 0 || !rep) return cudaSuccess;
-    fold_replicas_kernel<<<(n_hot + 255) / 256, 256, 0, s>>>(state, stride, hot_col, hot_rep, rep, n_hot);
-    return cudaGetLastError();
-}
-
-__global__ void encode_hot_kernel(int32_t *col_idx, int64_t nnz, const int *hot_id) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t c = col_idx[k];
-        const int h = hot_id[c];
-        if (h >= 0) col_idx[k] = -1 - h;
-    }
-}
-
-cudaError_t launch_encode_hot(int32_t *col_idx, int64_t nnz, const int *hot_id, cudaStream_t s) {
-    if (nnz <= 0) return cudaSuccess;
-    int64_t g = (nnz + 255) / 256;
-    if (g > 8192) g = 8192;
-    encode_hot_kernel<<<(int)g, 256, 0, s>>>(col_idx, nnz, hot_id);
-    return cudaGetLastError();
 }
 
 template <typename T, bool kDense>

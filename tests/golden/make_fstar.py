@@ -24,6 +24,9 @@ from paper_1606_04809_gb300 import synth  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
+BATCH = dict(count=256, seed=51, n_range=(1_000, 20_000), d_range=(100, 5_000), density_range=(0.005, 0.02),
+             lam_range=(1e-6, 1e-2), storage="bf16")
+
 WORKLOADS = {
     "rcv1like": lambda: synth.rcv1_like(),
     "urllike": lambda: synth.url_like(),
@@ -33,8 +36,29 @@ WORKLOADS = {
 SAMPLER_SEED = 30
 
 
+def batch_fstar():
+    """One certified f* per instance of the 256-instance batch workload."""
+    t0 = time.time()
+    ps = synth.logistic_batch(**BATCH)
+    items = []
+    for k, p in enumerate(ps):
+        res = R.certified_fstar(p, lambda ep, p=p: synth.sample_indices(p.n, p.n, SAMPLER_SEED, ep),
+                                rel_tol=1e-10, max_epochs=20000, check_every=10)
+        items.append({"fingerprint": p.fingerprint(), "lambda": p.lam, "fstar": res["fstar"],
+                      "bound": res["bound"], "epochs": res["epochs"]})
+        print(k, p.n, p.d, p.nnz, p.lam, res["epochs"], res["fstar"], flush=True)
+    out = {"name": "batch256", "generator": {k: list(v) if isinstance(v, tuple) else v for k, v in BATCH.items()},
+           "method": "serial float64 Sparse SAGA per instance, certified by |grad f|^2/(2 lambda)",
+           "instances": items, "seconds": time.time() - t0}
+    with open(os.path.join(HERE, "fstar_batch256.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def main(names):
     for name in names:
+        if name == "batch256":
+            batch_fstar()
+            continue
         t0 = time.time()
         p = WORKLOADS[name]()
         out = {"name": name, "problem": p.name, "fingerprint": p.fingerprint(), "lambda": p.lam,

@@ -86,19 +86,6 @@ def test_replay_long_rows_cross_the_register_tile():
     assert_replay(p, idx, "f32")
 
 
-@pytest.mark.parametrize("hot_target", [16, 10 ** 9])
-def test_replay_with_hot_columns_and_replica_slots(hot_target):
-    """Frequent columns (re-encoded hot ids, with or without replica slots) read and write
-    the same values as plain columns."""
-    p = synth.sparse_logistic(3000, 800, k_mean=60, k_min=1, k_max=400, k_sigma=0.8, zipf_s=1.1,
-                              values="abs_normal", storage="f32", seed=26)
-    idx = synth.sample_indices(p.n, p.n, seed=27)
-    (x, _, _), st, info = replay_pair(p, idx, "f32", hot_target=hot_target)
-    assert info["n_hot"] > 0
-    assert (info["replica_slots"] > 0) == (hot_target == 16)
-    assert rel(x, st.x) <= DET_TOL
-
-
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_replay_half_precision_storage(storage):
     p = synth.sparse_logistic(4000, 20000, k_mean=40, k_min=4, k_max=200, k_sigma=0.5, zipf_s=1.1,
@@ -200,7 +187,7 @@ def test_float64_evaluations_match(maker):
                                                zipf_s=1.1, storage="f32", seed=21),
          "hot": lambda: synth.sparse_logistic(20000, 3000, k_mean=40, k_min=1, k_max=300, k_sigma=0.6,
                                               zipf_s=1.1, storage="f32", seed=28)}[maker]()
-    with asaga.Context(p, seed=3, hot_target=64) as c:
+    with asaga.Context(p, seed=3) as c:
         asaga.asaga_run(c.ctx, 3)
         x, abar, alpha = asaga.asaga_get_state(c.ctx)
         f = asaga.asaga_objective(c.ctx)
@@ -258,19 +245,6 @@ def test_autotune_leaves_a_zero_state_and_rejects_deterministic_mode():
     with asaga.Context(p, deterministic=1) as c:
         with pytest.raises(asaga.AsagaError):
             asaga.asaga_autotune(c.ctx)
-
-
-def test_async_with_replica_slots_reaches_1e6():
-    """Spreading the reductions of frequent columns over replica slots keeps the
-    method's fixed point: the run still reaches the oracle's optimum."""
-    p = synth.rcv1_like(seed=29, n=60000, d=6000)
-    cert = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 30, ep), rel_tol=1e-10)
-    with asaga.Context(p, seed=3, abar_recompute_every=5, hot_target=4096, max_warps=256,
-                       gamma=0.5 / (3 * R.lipschitz(p))) as c:
-        info = asaga.asaga_get_info(c.ctx)
-        assert info["replica_slots"] > 100
-        s, r = asaga.asaga_run(c.ctx, 200, 1e-6, cert["fstar"])
-    assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict(), info)
 
 
 def test_async_dense_ridge_reaches_closed_form():

@@ -312,3 +312,34 @@ def test_sparsity_delta_brute_force():
     best = max(sum(1 for i in range(p.n) if v in set(p.col_idx[p.row_ptr[i]:p.row_ptr[i + 1]]))
                for v in range(p.d))
     assert R.sparsity_delta(p) == best / p.n
+
+
+def test_lipschitz_bounds_every_sampled_component():
+    """L bounds the largest Hessian eigenvalue of every sampled component
+    phi_i(a_i.x) + lambda/2 sum_{v in S_i} D_v x_v^2 (logistic curvature peaks
+    at z = 0 with 1/4) and is attained on a row whose heaviest term dominates:
+    here a row made of one column that no other row touches."""
+    p = tiny_sparse(n=12, d=9, k=3, seed=25, lam=0.3)
+    D = R.reweighting(p)
+    L = R.lipschitz(p)
+    A = R.csr(p).toarray()
+    worst = 0.0
+    for i in range(p.n):
+        mask = A[i] != 0
+        H = 0.25 * np.outer(A[i], A[i]) + p.lam * np.diag(D * mask)
+        worst = max(worst, np.linalg.eigvalsh(H).max())
+    assert worst <= L * (1 + 1e-12)
+    # a row of a single, otherwise unused column: eigenvalue = c a^2 + lambda n, exactly L
+    q = synth.Problem("rare", 3, 2, np.array([0, 1, 2, 3], dtype=np.int64), np.array([0, 0, 1], dtype=np.int32),
+                      np.array([0.5, 0.5, 0.1]), np.array([1.0, -1.0, 1.0]), "logistic", lam=0.5, storage="f64")
+    assert R.lipschitz(q) == pytest.approx(0.25 * 0.01 + 0.5 * 3, rel=1e-14)
+
+
+def test_serial_sparse_saga_is_stable_with_heavy_reweighting():
+    """With lambda n large and rare columns, gamma = 1/(3L) must account for
+    lambda D_v: the run converges to the Newton optimum."""
+    p = tiny_sparse(n=40, d=30, k=2, seed=26, lam=0.05)
+    assert p.lam * R.reweighting(p).max() > 0.25
+    xs = R.newton(p)
+    res = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 9, ep), rel_tol=1e-12, max_epochs=3000)
+    assert abs(res["fstar"] - R.objective(p, xs)) <= 1e-11 * abs(R.objective(p, xs))
