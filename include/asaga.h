@@ -191,14 +191,36 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  * float64 |grad f|^2 has shrunk by 1e-6 (or diverges, or reaches
  * trial_epochs epochs (<= 0: 40), or is already 1.5x slower than the best
  * trial).  Warp counts go from the resident maximum (at most n/4) down by
- * halves to 32; for each, steps gamma0 * 2^(-k/2) (gamma0 = options.gamma or
- * 1/(3L)) are tried from large to small until the time stops improving.
+ * halves to 4; for each, steps gamma0 * 2^(-k/2), k = -4..12 (gamma0 =
+ * options.gamma or 1/(3L); the paper's own grid reaches 10/L), are tried
+ * from large to small until the time stops improving.
  * The pair with the least update-kernel time wins; the step used is one
  * notch (1/sqrt 2) below the winning one, a margin for run-to-run variation
  * of asynchronous execution.  score = ln(1e6) / (winning time in seconds).
  * Leaves the state at x = 0, alpha = 0, abar = 0 (sampler position 0) with
  * the chosen pair in use.  EINVAL in deterministic mode. */
 asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);
+
+/* Overlap of the asynchronous updates (the tau of Assumption 1). */
+typedef struct {
+    int64_t updates;        /* updates traced                                        */
+    int warps;              /* concurrent warps of the run                           */
+    double tau_mean;        /* mean over updates of the number of others overlapping */
+    double tau_max;         /* largest such number                                   */
+    double tau_paper;       /* max over windows of 100 updates of the mean (App. E.2) */
+    double window_ns_mean;  /* mean time from an update's reads to its writes        */
+    double seconds;         /* device time of the traced launch                      */
+} asaga_overlap;
+
+/* Runs `epochs` epochs like asaga_run (same schedule; the state advances) while
+ * lane 0 of every warp records %globaltimer just before an update's reads and
+ * just after its writes are issued; two updates overlap when those intervals
+ * intersect.  tau_paper follows App. E.2: the average overlap over windows of
+ * 100 consecutive updates, maximised over windows (a lower bound on the true
+ * maximum).  Needs 16 bytes of scratch per update (allocated and freed on the
+ * context's stream) and no objective evaluation.  EINVAL: epochs <= 0, fewer
+ * than 2 updates, out NULL. */
+asaga_status asaga_measure_overlap(asaga_ctx *ctx, double epochs, asaga_overlap *out);
 
 /* Deterministic replay: runs one update per entry of idx (row indices in
  * [0,n)), strictly in order, on a single warp.  idx is a host pointer if
@@ -278,7 +300,7 @@ asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, c
 /* Per-instance step sizes from shared trials: the schedule is reset to the
  * default, and every trial runs all instances at once for trial_epochs
  * epochs (<= 0: 8) from x = 0 with gamma_i = s * gamma0_i, s on the ladder
- * 2^(-k/2); each instance keeps the s under which its float64 |grad f_i|^2
+ * 2^(-k/2), k = -4..8; each instance keeps the s under which its float64 |grad f_i|^2
  * fell most (decreasing over the last two epochs), one notch lower as a
  * margin.  Leaves every instance at x = 0.  results[i] may be NULL. */
 asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);

@@ -78,6 +78,15 @@ class asaga_tune_result(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class asaga_overlap(ctypes.Structure):
+    _fields_ = [("updates", ctypes.c_int64), ("warps", ctypes.c_int), ("tau_mean", ctypes.c_double),
+                ("tau_max", ctypes.c_double), ("tau_paper", ctypes.c_double), ("window_ns_mean", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _lib: Optional[ctypes.CDLL] = None
 
 
@@ -104,6 +113,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_run.argtypes = [vp, dbl, dbl, dbl, P(asaga_result)]
     L.asaga_run_indices.argtypes = [vp, vp, i64, i32]
     L.asaga_autotune.argtypes = [vp, dbl, P(asaga_tune_result)]
+    L.asaga_measure_overlap.argtypes = [vp, dbl, P(asaga_overlap)]
     L.asaga_objective.argtypes = [vp, P(dbl)]
     L.asaga_full_grad.argtypes = [vp, vp, P(dbl)]
     L.asaga_recompute_abar.argtypes = [vp, P(dbl)]
@@ -132,7 +142,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     for f in ("asaga_batch_create", "asaga_batch_run", "asaga_batch_autotune", "asaga_batch_set_schedule",
               "asaga_batch_get_state", "asaga_batch_get_info", "asaga_batch_objective"):
         getattr(L, f).restype = i32
-    for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_autotune", "asaga_objective", "asaga_full_grad",
+    for f in ("asaga_create", "asaga_run", "asaga_run_indices", "asaga_autotune", "asaga_measure_overlap", "asaga_objective", "asaga_full_grad",
               "asaga_recompute_abar", "asaga_get_state", "asaga_set_state", "asaga_get_info"):
         getattr(L, f).restype = i32
     _lib = L
@@ -226,6 +236,12 @@ def asaga_autotune(ctx: int, trial_epochs: float = 0.0) -> dict:
     r = asaga_tune_result()
     _check(ctx, load().asaga_autotune(ctx, float(trial_epochs), ctypes.byref(r)))
     return r.as_dict()
+
+
+def asaga_measure_overlap(ctx: int, epochs: float = 1.0) -> dict:
+    o = asaga_overlap()
+    _check(ctx, load().asaga_measure_overlap(ctx, float(epochs), ctypes.byref(o)))
+    return o.as_dict()
 
 
 def asaga_run_indices(ctx: int, idx, on_device: bool = False) -> None:

@@ -405,7 +405,8 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
             CK(cudaMemcpyAsync(c->col_idx, p->col_idx, c->nnz * sizeof(int32_t), kind, c->stream), "copy col_idx");
     }
     unsigned char *vals = nullptr;
-    TRY(dev_alloc(&vals, (size_t)c->nnz * vsz, c, err, "alloc values"));
+    // 64 bytes of slack: the update kernel stages 16-bit values as aligned 32-bit words
+    TRY(dev_alloc(&vals, (size_t)c->nnz * vsz + 64, c, err, "alloc values"));
     c->values = vals;
     const int in_dt = (int)p->values_dtype;
     const int want_dt = (int)o->storage_dtype;
@@ -544,6 +545,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.deadline_ns = 0;
     u.status = c->status;
+    u.trace = nullptr;
     return u;
 }
 
@@ -718,10 +720,10 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     cands.push_back((int)cap);
     int64_t w = 1;
     while (w * 2 < cap) w *= 2;
-    for (; w >= 32; w /= 2)
+    for (; w >= 4; w /= 2)
         if (w < cap) cands.push_back((int)w);
-    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2)
-    for (int k = 0; k <= 12; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
+    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2), from 4 gamma0 down to gamma0/64
+    for (int k = -4; k <= 12; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -775,6 +777,78 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         c->gamma = r.gamma;
     }
     if (res) *res = r;
+    return ASAGA_OK;
+}
+
+// Overlap of asynchronous updates (the tau of Assumption 1), measured as in
+// App. E.2: for each update, the number of other updates whose processing
+// interval (reads issued .. writes issued) intersects its own; tau_paper =
+// max over consecutive windows of 100 updates (in start order) of the
+// window's average overlap.
+asaga_status overlap_impl(asaga_ctx *c, double epochs, asaga_overlap *out, std::string *err) {
+    if (!out) return fail(err, ASAGA_EINVAL, "out is NULL");
+    if (!(epochs > 0) || !std::isfinite(epochs)) return fail(err, ASAGA_EINVAL, "epochs must be > 0");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    const int64_t count = (int64_t)std::llround(epochs * (double)c->n);
+    if (count < 2) return fail(err, ASAGA_EINVAL, "need at least 2 updates");
+    uint64_t *trace = nullptr;
+    CK(cudaMallocAsync((void **)&trace, 2 * count * sizeof(uint64_t), c->stream), "alloc trace");
+    UpdateParams u = update_params(c);
+    u.t_begin = (uint64_t)c->updates_done;
+    u.count = count;
+    u.trace = trace;
+    CK(cudaEventRecord(c->ev[0], c->stream), "event");
+    asaga_status st = launch_updates(c, u, err);
+    CK(cudaEventRecord(c->ev[1], c->stream), "event");
+    std::vector<uint64_t> h(2 * count);
+    if (st == ASAGA_OK) {
+        cudaError_t e = cudaMemcpyAsync(h.data(), trace, 2 * count * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                        c->stream);
+        if (e != cudaSuccess) st = cuda_fail(err, e, "copy trace");
+    }
+    cudaFreeAsync(trace, c->stream);
+    if (st != ASAGA_OK) return st;
+    TRY(stream_sync(c, err));
+    c->updates_done += count;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+    std::vector<uint64_t> starts(count), ends(count);
+    std::vector<int64_t> order(count);
+    double window_sum = 0;
+    for (int64_t t = 0; t < count; ++t) {
+        starts[t] = h[2 * t];
+        ends[t] = h[2 * t + 1];
+        order[t] = t;
+        window_sum += (double)(ends[t] - starts[t]);
+    }
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return starts[a] < starts[b]; });
+    std::vector<uint64_t> s_sorted(starts), e_sorted(ends);
+    std::sort(s_sorted.begin(), s_sorted.end());
+    std::sort(e_sorted.begin(), e_sorted.end());
+    // overlap(t) = #{r != t : start_r <= end_t and end_r >= start_t}
+    std::vector<double> ov(count);
+    double sum = 0, mx = 0;
+    for (int64_t k = 0; k < count; ++k) {
+        const int64_t t = order[k];
+        const int64_t started = std::upper_bound(s_sorted.begin(), s_sorted.end(), ends[t]) - s_sorted.begin();
+        const int64_t finished_before = std::lower_bound(e_sorted.begin(), e_sorted.end(), starts[t]) - e_sorted.begin();
+        ov[k] = (double)(started - finished_before - 1);
+        sum += ov[k];
+        mx = std::max(mx, ov[k]);
+    }
+    double paper = 0;
+    for (int64_t k = 0; k + 100 <= count; k += 100) {
+        double w = 0;
+        for (int64_t j = k; j < k + 100; ++j) w += ov[j];
+        paper = std::max(paper, w / 100.0);
+    }
+    out->updates = count;
+    out->warps = c->warps;
+    out->tau_mean = sum / (double)count;
+    out->tau_max = mx;
+    out->tau_paper = paper;
+    out->window_ns_mean = window_sum / (double)count;
+    out->seconds = ms * 1e-3;
     return ASAGA_OK;
 }
 
@@ -1075,7 +1149,7 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
     TRY(grads(g0));
     int trials = 0;
     double seconds = 0;
-    for (int k = 0; k <= 8; ++k) {
+    for (int k = -4; k <= 8; ++k) {  // step ladder 4 gamma0 ... gamma0/16
         const double scale = std::pow(2.0, -0.5 * k);
         for (auto *c : b->ctx) TRY(reset_state(c, err));
         std::vector<double> g1(b->count), g2(b->count), g3(b->count);
@@ -1181,6 +1255,11 @@ asaga_status asaga_run(asaga_ctx *c, double max_epochs, double target, double f_
 asaga_status asaga_autotune(asaga_ctx *c, double trial_epochs, asaga_tune_result *res) {
     if (!c) return ASAGA_EINVAL;
     return autotune_impl(c, trial_epochs, res, &c->err);
+}
+
+asaga_status asaga_measure_overlap(asaga_ctx *c, double epochs, asaga_overlap *out) {
+    if (!c) return ASAGA_EINVAL;
+    return overlap_impl(c, epochs, out, &c->err);
 }
 
 asaga_status asaga_run_indices(asaga_ctx *c, const int64_t *idx, int64_t count, int idx_on_device) {

@@ -40,6 +40,7 @@ struct UpdateParams {
     int fence_each;           // 1: fence after every update (single-warp order)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     int *status;              // bit 0: timed out, bit 1: bad index
+    uint64_t *trace;          // 2 * count: %globaltimer before the reads / after the writes of update t (or nullptr)
 };
 
 // Float64 evaluation parameters (objective, gradient, abar recomputation).

@@ -14,64 +14,71 @@
 // abar = (1/n) sum_i alpha_i a_i holds in exact arithmetic under any
 // interleaving of warps.
 //
-// Latency: the CSR slice of a row does not depend on the solver state, so a
-// warp requests the column indices and values of a row two rows before it
-// processes it (and the row_ptr entries three rows before); the window
-// between reading x^ and writing x, which sets the overlap tau, is then one
-// L2 gather, a warp reduction and the reductions back to L2.
+// Latency: a row's CSR data does not depend on the solver state, so each
+// warp stages it in shared memory ahead of time with asynchronous copies
+// (cp.async, one commit group per update): the row_ptr entries and label of
+// the row four updates ahead and the column indices and values of the row
+// two updates ahead are in flight while the current row is processed.
+// Commit groups complete in order, so waiting for all but the newest group
+// makes exactly the rows needed next available.  The window between reading
+// x^ and writing x, which sets the overlap tau, is then one L2 gather, a
+// warp reduction and the reductions back to L2.
 //
 // Layout: A in CSR (int64 row_ptr, int32 col_idx, values in fp32/bf16/fp16)
 // or dense row-major; per-column state float4 {x, abar, D, 0}, so one
 // 16-byte L2 read serves x^_v, abar_v and D_v and one 8-byte vector
-// reduction updates x_v and abar_v.  Up to 32 * kSlots entries of a row are
-// held in registers (lane l owns entries l, l+32, ...); longer rows read
-// the remainder again from memory.
+// reduction updates x_v and abar_v.  Up to kRowCap entries of a row are
+// staged (lane l owns entries l, l+32, ...); longer rows read the rest
+// from global memory.
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
 namespace asaga {
 
 constexpr int kSlots = 4;
+constexpr int kRowCap = 32 * kSlots;  // entries of a row staged in shared memory
+constexpr int kStages = 4;            // staged CSR slices per warp (ring)
+constexpr int kMetaRing = 8;          // staged row_ptr / label entries per warp (ring)
 
-// The part of a row that does not depend on the solver state.
-struct RowData {
-    int64_t start;
-    int len;
-    float label;
-    int c[kSlots];
-    float a[kSlots];
+// Per-warp staging area in shared memory (4.3 KB).
+struct __align__(16) WarpRing {
+    int64_t start[kMetaRing];  // row_ptr[i]
+    int64_t end[kMetaRing];    // row_ptr[i + 1]
+    int64_t row[kMetaRing];    // i, or -1 past the end
+    float label[kMetaRing];
+    int32_t col[kStages][kRowCap];
+    uint32_t val[kStages][kRowCap];  // raw 32-bit words: one fp32 or two 16-bit values
 };
 
 __device__ __forceinline__ void red_add_f32(float *p, float v) {
     asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 
-template <bool kDense>
-__device__ __forceinline__ void load_meta(const UpdateParams &P, int64_t i, RowData &r) {
-    if (kDense) {
-        r.start = i * P.d;
-        r.len = (int)P.d;
-    } else {
-        const int64_t s = __ldg(P.row_ptr + i);
-        r.start = s;
-        r.len = (int)(__ldg(P.row_ptr + i + 1) - s);
-    }
-    r.label = __ldg(P.labels + i);
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_newest() {
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <typename T, bool kDense>
-__device__ __forceinline__ void load_slots(const UpdateParams &P, const T *__restrict__ vals, RowData &r,
-                                           int lane) {
-#pragma unroll
-    for (int s = 0; s < kSlots; ++s) {
-        const int k = lane + 32 * s;
-        r.c[s] = 0;
-        r.a[s] = 0.f;
-        if (k < r.len) {
-            r.c[s] = kDense ? k : ld_stream(P.col_idx + r.start + k);
-            r.a[s] = to_f32(ld_stream(vals + r.start + k));
-        }
-    }
+template <typename T> __device__ __forceinline__ float staged_value(const uint32_t *words, int64_t start, int k);
+template <> __device__ __forceinline__ float staged_value<float>(const uint32_t *words, int64_t, int k) {
+    return __uint_as_float(words[k]);
+}
+template <> __device__ __forceinline__ float staged_value<__nv_bfloat16>(const uint32_t *words, int64_t start, int k) {
+    const unsigned short h = reinterpret_cast<const unsigned short *>(words)[(int)(start & 1) + k];
+    return __uint_as_float((unsigned)h << 16);
+}
+template <> __device__ __forceinline__ float staged_value<__half>(const uint32_t *words, int64_t start, int k) {
+    const unsigned short h = reinterpret_cast<const unsigned short *>(words)[(int)(start & 1) + k];
+    return __half2float(__ushort_as_half(h));
 }
 
 // Row of update t of this launch, or -1 past the end (or on a bad index).
@@ -88,39 +95,89 @@ __device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool
     return sample_row(P.seed, P.t_begin + (uint64_t)t, P.n);
 }
 
+// Lane 0 requests row i's row_ptr entries and label into meta slot m.
+template <bool kDense>
+__device__ __forceinline__ void stage_meta(const UpdateParams &P, WarpRing &R, int m, int64_t i, int lane) {
+    if (lane != 0) return;
+    R.row[m] = i;
+    if (i < 0) return;
+    if (kDense) {
+        R.start[m] = i * P.d;
+        R.end[m] = i * P.d + P.d;
+    } else {
+        cp_async8(&R.start[m], P.row_ptr + i);
+        cp_async8(&R.end[m], P.row_ptr + i + 1);
+    }
+    cp_async4(&R.label[m], P.labels + i);
+}
+
+// All lanes request the first kRowCap column indices and values of the row in
+// meta slot m into stage st (16-bit values travel as aligned 32-bit words).
 template <typename T, bool kDense>
-__device__ __forceinline__ void process_row(const UpdateParams &P, const T *__restrict__ vals, int64_t i,
-                                            const RowData &r, int lane) {
+__device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, int m, int st, int lane) {
+    if (R.row[m] < 0) return;
+    const int64_t start = R.start[m];
+    const int len = (int)(R.end[m] - start);
+    const int cnt = len < kRowCap ? len : kRowCap;
+    if (!kDense)
+        for (int j = lane; j < cnt; j += 32) cp_async4(&R.col[st][j], P.col_idx + start + j);
+    if (sizeof(T) == 4) {
+        const uint32_t *w = static_cast<const uint32_t *>(P.values);
+        for (int j = lane; j < cnt; j += 32) cp_async4(&R.val[st][j], w + start + j);
+    } else {
+        const uint32_t *w = static_cast<const uint32_t *>(P.values);
+        const int64_t w0 = start >> 1;
+        const int nw = (int)(((start + cnt + 1) >> 1) - w0);
+        for (int j = lane; j < nw; j += 32) cp_async4(&R.val[st][j], w + w0 + j);
+    }
+}
+
+template <typename T, bool kDense>
+__device__ __forceinline__ void process_row(const UpdateParams &P, const WarpRing &R, int m, int st, int lane) {
+    const T *__restrict__ vals = static_cast<const T *>(P.values);
+    const int64_t i = R.row[m];
+    const int64_t start = R.start[m];
+    const int len = (int)(R.end[m] - start);
+    const float label = R.label[m];
     const float4 *__restrict__ state = P.state;
     const int64_t stride = P.stride;
+    int c[kSlots];
+    float a[kSlots];
     float4 s[kSlots];
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
+        const int k = lane + 32 * q;
+        c[q] = 0;
+        a[q] = 0.f;
         s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lane + 32 * q < r.len) s[q] = ld_state(state + r.c[q] * stride);
+        if (k < len) {
+            c[q] = kDense ? k : R.col[st][k];
+            a[q] = staged_value<T>(R.val[st], start, k);
+            s[q] = ld_state(state + c[q] * stride);
+        }
     }
     const float alpha_hat = __ldcg(P.alpha + i);
     float z = 0.f;
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) z = fmaf(r.a[q], s[q].x, z);
-    for (int k = lane + 32 * kSlots; k < r.len; k += 32) {  // rest of a long row
-        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
-        z = fmaf(to_f32(ld_stream(vals + r.start + k)), ld_state(state + cc * stride).x, z);
+    for (int q = 0; q < kSlots; ++q) z = fmaf(a[q], s[q].x, z);
+    for (int k = lane + kRowCap; k < len; k += 32) {  // rest of a long row
+        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
+        z = fmaf(to_f32(ld_stream(vals + start + k)), ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
-    const float delta = phi_prime_f32(P.loss, z, r.label) - alpha_hat;  // same value in every lane
+    const float delta = phi_prime_f32(P.loss, z, label) - alpha_hat;  // same value in every lane
 
     const float gamma = P.gamma, lambda = P.lambda, inv_n = P.inv_n;
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
-        if (lane + 32 * q < r.len) {
-            const float dx = -gamma * fmaf(delta, r.a[q], s[q].z * fmaf(lambda, s[q].x, s[q].y));
-            red_add_v2(P.state + r.c[q] * stride, dx, delta * r.a[q] * inv_n);
+        if (lane + 32 * q < len) {
+            const float dx = -gamma * fmaf(delta, a[q], s[q].z * fmaf(lambda, s[q].x, s[q].y));
+            red_add_v2(P.state + c[q] * stride, dx, delta * a[q] * inv_n);
         }
     }
-    for (int k = lane + 32 * kSlots; k < r.len; k += 32) {
-        const int cc = kDense ? k : ld_stream(P.col_idx + r.start + k);
-        const float av = to_f32(ld_stream(vals + r.start + k));
+    for (int k = lane + kRowCap; k < len; k += 32) {
+        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
+        const float av = to_f32(ld_stream(vals + start + k));
         const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
         red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
@@ -129,41 +186,45 @@ __device__ __forceinline__ void process_row(const UpdateParams &P, const T *__re
 }
 
 // One warp's share of a launch: updates warp, warp + W, warp + 2W, ... of P.
+// Iteration k processes the row of update warp + k W; before it, all commit
+// groups but the newest are complete, which covers that row's staged slice
+// and the row_ptr entries of row k + 2, whose slice is requested next.
 template <typename T, bool kDense>
-__device__ __forceinline__ void warp_updates(const UpdateParams &P, int warp, int lane) {
-    const T *__restrict__ vals = static_cast<const T *>(P.values);
+__device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R, int warp, int lane) {
     const int64_t W = P.nwarps;
-
     uint64_t deadline = 0;
     if (P.deadline_ns) {  // budget relative to this warp's start (warp-uniform)
         const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
         deadline = now + P.deadline_ns;
     }
     bool bad = false;
-    // Software pipeline over this warp's rows with four register buffers
-    // whose roles rotate by unrolling (no buffer is ever copied, so no copy
-    // waits on a load in flight): in each step the row in X is processed,
-    // Y's CSR slice is in flight since the previous step, Z's slice is
-    // requested (its row_ptr entries arrived during the previous step) and
-    // V's row_ptr entries are requested.
-    int64_t t = warp;
-    RowData rA, rB, rC, rD;
-    int64_t iA = row_of(P, t, bad);
-    int64_t iB = iA >= 0 ? row_of(P, t + W, bad) : -1;
-    int64_t iC = iB >= 0 ? row_of(P, t + 2 * W, bad) : -1;
-    int64_t iD = -1;
-    if (iA >= 0) load_meta<kDense>(P, iA, rA);
-    if (iB >= 0) load_meta<kDense>(P, iB, rB);
-    if (iC >= 0) load_meta<kDense>(P, iC, rC);
-    if (iA >= 0) load_slots<T, kDense>(P, vals, rA, lane);
-    if (iB >= 0) load_slots<T, kDense>(P, vals, rB, lane);
+    // prologue: row_ptr entries of rows 0..3, then the slices of rows 0 and 1
+    for (int k = 0; k < 4; ++k) stage_meta<kDense>(P, R, k, row_of(P, warp + k * W, bad), lane);
+    cp_async_wait_all();
+    __syncwarp();
+    stage_slice<T, kDense>(P, R, 0, 0, lane);
+    cp_async_commit();
+    stage_slice<T, kDense>(P, R, 1, 1, lane);
+    cp_async_commit();
     int64_t done = 0;
-    bool stop = false;
-    auto step = [&](int64_t iX, const RowData &X, int64_t iZ, RowData &Z, int64_t &iV, RowData &V) {
-        if (iZ >= 0) load_slots<T, kDense>(P, vals, Z, lane);
-        iV = iZ >= 0 ? row_of(P, t + 3 * W, bad) : -1;
-        if (iV >= 0) load_meta<kDense>(P, iV, V);
-        process_row<T, kDense>(P, vals, iX, X, lane);
+    for (int64_t k = 0;; ++k) {
+        cp_async_wait_all_but_newest();
+        __syncwarp();
+        const int m = (int)(k & (kMetaRing - 1));
+        if (R.row[m] < 0) break;
+        const int m2 = (int)((k + 2) & (kMetaRing - 1));
+        stage_slice<T, kDense>(P, R, m2, (int)((k + 2) & (kStages - 1)), lane);
+        const bool more = R.row[(k + 3) & (kMetaRing - 1)] >= 0;
+        stage_meta<kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
+                           lane);
+        cp_async_commit();
+        uint64_t t_read = 0;
+        if (P.trace) t_read = globaltimer_ns();
+        process_row<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane);
+        if (P.trace && lane == 0) {
+            P.trace[2 * (warp + k * W)] = t_read;
+            P.trace[2 * (warp + k * W) + 1] = globaltimer_ns();
+        }
         if (P.fence_each) {
             __threadfence();
             __syncwarp();
@@ -172,32 +233,21 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, int warp, in
             const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
             if (now > deadline) {
                 if (lane == 0) atomicOr(P.status, 1);
-                stop = true;
+                break;
             }
         }
-        t += W;
-    };
-#pragma unroll 1
-    while (true) {
-        if (iA < 0 || stop) break;
-        step(iA, rA, iC, rC, iD, rD);
-        if (iB < 0 || stop) break;
-        step(iB, rB, iD, rD, iA, rA);
-        if (iC < 0 || stop) break;
-        step(iC, rC, iA, rA, iB, rB);
-        if (iD < 0 || stop) break;
-        step(iD, rD, iB, rB, iC, rC);
     }
-    if (stop) return;
+    cp_async_wait_all();  // no copy may outlive the warp's staging area
     if (bad && lane == 0) atomicOr(P.status, 2);
 }
 
 template <typename T, bool kDense>
-__global__ void __launch_bounds__(kUpdateBlock, 2) update_kernel(const UpdateParams P) {
+__global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams P) {
+    __shared__ WarpRing rings[kUpdateBlock / 32];
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= P.nwarps) return;
-    warp_updates<T, kDense>(P, warp, lane);
+    warp_updates<T, kDense>(P, rings[threadIdx.x >> 5], warp, lane);
 }
 
 // Many independent problems in one launch: block b serves instance
@@ -208,6 +258,7 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
                                                                    const int *__restrict__ block_begin, int count) {
     __shared__ UpdateParams sp;
     __shared__ int s_inst;
+    __shared__ WarpRing rings[kBatchBlock / 32];
     if (threadIdx.x == 0) {
         int lo = 0, hi = count - 1;  // binary search: last instance whose first block <= blockIdx.x
         while (lo < hi) {
@@ -221,7 +272,7 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((blockIdx.x - block_begin[s_inst]) * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= sp.nwarps || sp.count <= 0) return;
-    warp_updates<T, kDense>(sp, warp, lane);
+    warp_updates<T, kDense>(sp, rings[threadIdx.x >> 5], warp, lane);
 }
 
 template <typename T, bool kDense>

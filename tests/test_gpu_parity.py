@@ -313,3 +313,19 @@ def test_torch_stream_is_used():
     with asaga.Context(p, seed=9, cuda_stream=s.cuda_stream) as c:
         st, r = asaga.asaga_run(c.ctx, 2)
         assert st == asaga.OK and np.isfinite(r.f_last)
+
+
+def test_overlap_is_zero_for_one_warp_and_grows_with_warps():
+    """tau (App. E.2 estimator): a single warp never overlaps itself; W warps
+    keep about W - 1 other updates in flight."""
+    p = synth.rcv1_like(seed=30, n=40000, d=4000)
+    with asaga.Context(p, seed=1, max_warps=1) as c:
+        o = asaga.asaga_measure_overlap(c.ctx, 0.05)
+        assert o["warps"] == 1 and o["updates"] == 2000
+        assert o["tau_mean"] <= 0.05
+    with asaga.Context(p, seed=1, max_warps=256) as c:
+        o = asaga.asaga_measure_overlap(c.ctx, 1.0)
+        assert o["warps"] == 256
+        assert 0.3 * 255 <= o["tau_mean"] <= 3 * 256, o
+        assert o["tau_paper"] >= o["tau_mean"] and o["tau_max"] >= o["tau_paper"]
+        assert o["window_ns_mean"] > 0
