@@ -526,6 +526,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     UpdateParams u;
     u.n = c->n;
     u.d = c->d;
+    u.nnz = c->nnz;
     u.row_ptr = c->row_ptr;
     u.col_idx = c->col_idx;
     u.values = c->values;
@@ -608,6 +609,11 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
         r.f_last = c->hout[0];
         if (c->abar_every > 0 && seg % c->abar_every == 0) r.abar_drift = c->hout[1];
         if (target > 0 || std::isfinite(f_star)) r.rel_subopt = (r.f_last - f_star) / std::fabs(f_star);
+        if (*c->hstatus & 4) {
+            st = ASAGA_ECUDA;
+            fail(err, st, "update kernel found a malformed row range");
+            break;
+        }
         if (*c->hstatus & 1) {
             st = ASAGA_ETIMEOUT;
             fail(err, st, "timeout");

@@ -23,6 +23,7 @@ enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3 };
 // sampled row, Algorithm 2).
 struct UpdateParams {
     int64_t n, d;
+    int64_t nnz;              // entries of A (n*d for dense); staged row ranges are checked against it
     const int64_t *row_ptr;   // n+1 (sparse) or nullptr (dense)
     const int32_t *col_idx;   // nnz (sparse) or nullptr (dense)
     const void *values;       // nnz (or n*d) of the storage type
@@ -39,7 +40,7 @@ struct UpdateParams {
     const int64_t *idx;       // explicit row sequence (deterministic replay) or nullptr
     int fence_each;           // 1: fence after every update (single-warp order)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
-    int *status;              // bit 0: timed out, bit 1: bad index
+    int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range
     uint64_t *trace;          // 2 * count: %globaltimer before the reads / after the writes of update t (or nullptr)
 };
 

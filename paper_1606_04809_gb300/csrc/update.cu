@@ -66,7 +66,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all_but_newest() {
     asm volatile("cp.async.wait_group 1;" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Commits every copy this thread has issued and waits for all of them.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T> __device__ __forceinline__ float staged_value(const uint32_t *words, int64_t start, int k);
 template <> __device__ __forceinline__ float staged_value<float>(const uint32_t *words, int64_t, int k) {
@@ -117,7 +118,12 @@ template <typename T, bool kDense>
 __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, int m, int st, int lane) {
     if (R.row[m] < 0) return;
     const int64_t start = R.start[m];
-    const int len = (int)(R.end[m] - start);
+    const int64_t end = R.end[m];
+    if (start < 0 || end < start || end > P.nnz) {  // a malformed row range: record it, copy nothing
+        if (lane == 0) atomicOr(P.status, 4);
+        return;
+    }
+    const int len = (int)(end - start);
     const int cnt = len < kRowCap ? len : kRowCap;
     if (!kDense)
         for (int j = lane; j < cnt; j += 32) cp_async4(&R.col[st][j], P.col_idx + start + j);
@@ -137,6 +143,7 @@ __device__ __forceinline__ void process_row(const UpdateParams &P, const WarpRin
     const T *__restrict__ vals = static_cast<const T *>(P.values);
     const int64_t i = R.row[m];
     const int64_t start = R.start[m];
+    if (start < 0 || R.end[m] < start || R.end[m] > P.nnz) return;  // recorded when it was staged
     const int len = (int)(R.end[m] - start);
     const float label = R.label[m];
     const float4 *__restrict__ state = P.state;
