@@ -193,7 +193,9 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  * trial).  Warp counts go from the resident maximum (at most n/4) down by
  * halves to 4; for each, steps gamma0 * 2^(-k/2), k = -4..12 (gamma0 =
  * options.gamma or 1/(3L); the paper's own grid reaches 10/L), are tried
- * from large to small until the time stops improving.
+ * from large to small until the time stops improving -- starting at gamma0
+ * for the largest warp count and two notches above the previous winner for
+ * each smaller one (fewer warps overlap less, so larger steps can be stable).
  * The pair with the least update-kernel time wins; the step used is one
  * notch (1/sqrt 2) below the winning one, a margin for run-to-run variation
  * of asynchronous execution.  score = ln(1e6) / (winning time in seconds).

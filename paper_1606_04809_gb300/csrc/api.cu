@@ -741,7 +741,8 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     TRY(stream_sync(c, err));
     const double g0 = c->hout[2];
     double best_ms = INFINITY;
-    size_t best_k = 0, first_k = 0;
+    size_t best_k = 0;
+    size_t first_k = 4;  // the first (largest) warp count starts at gamma0 itself
     for (int W : cands) {
         double w_best = INFINITY;
         long w_k = -1;

@@ -74,11 +74,14 @@ __device__ __forceinline__ int64_t sample_row(uint64_t seed, uint64_t t, int64_t
 }
 
 // phi'(z) in float32.  Logistic: -b / (1 + exp(b z)); squared: z - y.
+// exp(-|t|) lies in (0, 1], where CUDA's fast __expf is within a few ulp;
+// the division uses the correctly rounded reciprocal.
 __device__ __forceinline__ float phi_prime_f32(int loss, float z, float b) {
     if (loss == 0) {
-        float t = b * z;
-        float e = expf(-fabsf(t));                       // in (0, 1]
-        float s = (t >= 0.f) ? e / (1.f + e) : 1.f / (1.f + e);  // 1 / (1 + exp(t))
+        const float t = b * z;
+        const float e = __expf(-fabsf(t));     // in (0, 1]
+        const float r = __frcp_rn(1.f + e);    // 1 / (1 + e)
+        const float s = (t >= 0.f) ? e * r : r;  // 1 / (1 + exp(t))
         return -b * s;
     }
     return z - b;

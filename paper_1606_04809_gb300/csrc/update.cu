@@ -18,7 +18,8 @@
 // warp stages it in shared memory ahead of time with asynchronous copies
 // (cp.async, one commit group per update): the row_ptr entries and label of
 // the row four updates ahead and the column indices and values of the row
-// two updates ahead are in flight while the current row is processed.
+// two updates ahead are requested while the current row's state reads are
+// in flight.
 // Commit groups complete in order, so waiting for all but the newest group
 // makes exactly the rows needed next available.  The window between reading
 // x^ and writing x, which sets the overlap tau, is then one L2 gather, a
@@ -138,58 +139,75 @@ __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, 
     }
 }
 
-template <typename T, bool kDense>
-__device__ __forceinline__ void process_row(const UpdateParams &P, const WarpRing &R, int m, int st, int lane) {
-    const T *__restrict__ vals = static_cast<const T *>(P.values);
-    const int64_t i = R.row[m];
-    const int64_t start = R.start[m];
-    if (start < 0 || R.end[m] < start || R.end[m] > P.nnz) return;  // recorded when it was staged
-    const int len = (int)(R.end[m] - start);
-    const float label = R.label[m];
-    const float4 *__restrict__ state = P.state;
-    const int64_t stride = P.stride;
+// The state-dependent part of one update, split in two so that the staging
+// of later rows runs while the gathers are in flight.
+template <bool kDense> struct Update {
+    int64_t i, start;
+    int len;
+    float label, alpha_hat;
     int c[kSlots];
     float a[kSlots];
     float4 s[kSlots];
+};
+
+// Reads the staged row and issues the inconsistent reads of x^, abar, D and alpha^_i.
+template <typename T, bool kDense>
+__device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRing &R, int m, int st, int lane,
+                                             Update<kDense> &u) {
+    u.i = R.row[m];
+    u.start = R.start[m];
+    const int64_t end = R.end[m];
+    if (u.start < 0 || end < u.start || end > P.nnz) return false;  // recorded when it was staged
+    u.len = (int)(end - u.start);
+    u.label = R.label[m];
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
         const int k = lane + 32 * q;
-        c[q] = 0;
-        a[q] = 0.f;
-        s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < len) {
-            c[q] = kDense ? k : R.col[st][k];
-            a[q] = staged_value<T>(R.val[st], start, k);
-            s[q] = ld_state(state + c[q] * stride);
+        u.c[q] = 0;
+        u.a[q] = 0.f;
+        u.s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < u.len) {
+            u.c[q] = kDense ? k : R.col[st][k];
+            u.a[q] = staged_value<T>(R.val[st], u.start, k);
+            u.s[q] = ld_state(P.state + u.c[q] * (int64_t)P.stride);
         }
     }
-    const float alpha_hat = __ldcg(P.alpha + i);
+    u.alpha_hat = __ldcg(P.alpha + u.i);
+    return true;
+}
+
+// Dot product, loss derivative and the atomic adds to x, abar and alpha_i.
+template <typename T, bool kDense>
+__device__ __forceinline__ void finish_update(const UpdateParams &P, const Update<kDense> &u, int lane) {
+    const T *__restrict__ vals = static_cast<const T *>(P.values);
+    const float4 *__restrict__ state = P.state;
+    const int64_t stride = P.stride;
     float z = 0.f;
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) z = fmaf(a[q], s[q].x, z);
-    for (int k = lane + kRowCap; k < len; k += 32) {  // rest of a long row
-        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
-        z = fmaf(to_f32(ld_stream(vals + start + k)), ld_state(state + cc * stride).x, z);
+    for (int q = 0; q < kSlots; ++q) z = fmaf(u.a[q], u.s[q].x, z);
+    for (int k = lane + kRowCap; k < u.len; k += 32) {  // rest of a long row
+        const int cc = kDense ? k : ld_stream(P.col_idx + u.start + k);
+        z = fmaf(to_f32(ld_stream(vals + u.start + k)), ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
-    const float delta = phi_prime_f32(P.loss, z, label) - alpha_hat;  // same value in every lane
+    const float delta = phi_prime_f32(P.loss, z, u.label) - u.alpha_hat;  // same value in every lane
 
     const float gamma = P.gamma, lambda = P.lambda, inv_n = P.inv_n;
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
-        if (lane + 32 * q < len) {
-            const float dx = -gamma * fmaf(delta, a[q], s[q].z * fmaf(lambda, s[q].x, s[q].y));
-            red_add_v2(P.state + c[q] * stride, dx, delta * a[q] * inv_n);
+        if (lane + 32 * q < u.len) {
+            const float dx = -gamma * fmaf(delta, u.a[q], u.s[q].z * fmaf(lambda, u.s[q].x, u.s[q].y));
+            red_add_v2(P.state + u.c[q] * stride, dx, delta * u.a[q] * inv_n);
         }
     }
-    for (int k = lane + kRowCap; k < len; k += 32) {
-        const int cc = kDense ? k : ld_stream(P.col_idx + start + k);
-        const float av = to_f32(ld_stream(vals + start + k));
+    for (int k = lane + kRowCap; k < u.len; k += 32) {
+        const int cc = kDense ? k : ld_stream(P.col_idx + u.start + k);
+        const float av = to_f32(ld_stream(vals + u.start + k));
         const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
         red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
     }
-    if (lane == 0) red_add_f32(P.alpha + i, delta);
+    if (lane == 0) red_add_f32(P.alpha + u.i, delta);
 }
 
 // One warp's share of a launch: updates warp, warp + W, warp + 2W, ... of P.
@@ -219,15 +237,18 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
         __syncwarp();
         const int m = (int)(k & (kMetaRing - 1));
         if (R.row[m] < 0) break;
+        uint64_t t_read = 0;
+        if (P.trace) t_read = globaltimer_ns();
+        Update<kDense> u;
+        const bool ok = begin_update<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u);
+        // while the reads are in flight: stage the slice of row k + 2 and the row_ptr entries of row k + 4
         const int m2 = (int)((k + 2) & (kMetaRing - 1));
         stage_slice<T, kDense>(P, R, m2, (int)((k + 2) & (kStages - 1)), lane);
         const bool more = R.row[(k + 3) & (kMetaRing - 1)] >= 0;
         stage_meta<kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
                            lane);
         cp_async_commit();
-        uint64_t t_read = 0;
-        if (P.trace) t_read = globaltimer_ns();
-        process_row<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane);
+        if (ok) finish_update<T, kDense>(P, u, lane);
         if (P.trace && lane == 0) {
             P.trace[2 * (warp + k * W)] = t_read;
             P.trace[2 * (warp + k * W) + 1] = globaltimer_ns();
