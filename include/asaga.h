@@ -101,6 +101,10 @@ typedef struct {
  *   column_stride        spacing of the per-column state in 16-byte units
  *                        (1 = packed; 8 = one 128-byte line per column, which
  *                        spreads atomics on very small d); 0 = automatic.
+ *   plain_writes         1 = replace the atomic adds by non-thread-safe
+ *                        load-add-store updates, which lose concurrent adds:
+ *                        the comparison of App. G.2 ("Necessity of
+ *                        compare-and-swap"), for diagnostics only; 0 = atomic.
  */
 typedef struct {
     asaga_loss loss;
@@ -115,6 +119,7 @@ typedef struct {
     double timeout_s;
     void *cuda_stream;
     int column_stride;
+    int plain_writes;
 } asaga_options;
 
 /* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and

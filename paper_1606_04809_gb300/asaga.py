@@ -47,7 +47,8 @@ class asaga_options(ctypes.Structure):
                 ("storage_dtype", ctypes.c_int), ("max_warps", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("epochs_per_segment", ctypes.c_int),
                 ("abar_recompute_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int)]
+                ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int),
+                ("plain_writes", ctypes.c_int)]
 
 
 class asaga_result(ctypes.Structure):

@@ -34,6 +34,7 @@ struct asaga_ctx {
     int resident_warps = 1;
     double gamma_base = 0;  // options.gamma, or 1/(3L)
     bool deterministic = false;
+    bool plain_writes = false;
     uint64_t seed = 0;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -386,6 +387,7 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     c->vtype = o->storage_dtype == ASAGA_F32 ? kF32 : (o->storage_dtype == ASAGA_BF16 ? kBF16 : kF16);
     c->lambda = o->lambda;
     c->deterministic = o->deterministic != 0;
+    c->plain_writes = o->plain_writes != 0;
     c->seed = o->seed;
     c->epochs_per_segment = o->epochs_per_segment > 0 ? o->epochs_per_segment : 1;
     c->abar_every = o->abar_recompute_every;
@@ -544,6 +546,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.nwarps = c->warps;
     u.idx = nullptr;
     u.fence_each = c->warps == 1 ? 1 : 0;
+    u.plain_writes = c->plain_writes ? 1 : 0;
     u.deadline_ns = 0;
     u.status = c->status;
     u.trace = nullptr;
@@ -1230,6 +1233,7 @@ void asaga_default_options(asaga_options *o) {
     o->timeout_s = 0.0;
     o->cuda_stream = nullptr;
     o->column_stride = 0;
+    o->plain_writes = 0;
 }
 
 asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {

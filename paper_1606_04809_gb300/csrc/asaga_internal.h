@@ -39,6 +39,7 @@ struct UpdateParams {
     int nwarps;               // warps taking part (static strided split)
     const int64_t *idx;       // explicit row sequence (deterministic replay) or nullptr
     int fence_each;           // 1: fence after every update (single-warp order)
+    int plain_writes;         // 1: non-atomic load-add-store instead of reductions (diagnostic)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range
     uint64_t *trace;          // 2 * count: %globaltimer before the reads / after the writes of update t (or nullptr)

@@ -18,8 +18,8 @@
 // warp stages it in shared memory ahead of time with asynchronous copies
 // (cp.async, one commit group per update): the row_ptr entries and label of
 // the row four updates ahead and the column indices and values of the row
-// two updates ahead are requested while the current row's state reads are
-// in flight.
+// two updates ahead are requested just before the current row is processed,
+// outside the window between its state reads and writes.
 // Commit groups complete in order, so waiting for all but the newest group
 // makes exactly the rows needed next available.  The window between reading
 // x^ and writing x, which sets the overlap tau, is then one L2 gather, a
@@ -139,8 +139,9 @@ __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, 
     }
 }
 
-// The state-dependent part of one update, split in two so that the staging
-// of later rows runs while the gathers are in flight.
+// The state-dependent part of one update: the inconsistent reads
+// (begin_update), then the dot product, loss derivative and atomic adds
+// (finish_update).
 template <bool kDense> struct Update {
     int64_t i, start;
     int len;
@@ -193,6 +194,19 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
     const float delta = phi_prime_f32(P.loss, z, u.label) - u.alpha_hat;  // same value in every lane
 
     const float gamma = P.gamma, lambda = P.lambda, inv_n = P.inv_n;
+    if (P.plain_writes) {  // non-thread-safe x_v = x_v + dx (App. G.2 comparison): concurrent adds can be lost
+#pragma unroll
+        for (int q = 0; q < kSlots; ++q) {
+            if (lane + 32 * q < u.len) {
+                const float dx = -gamma * fmaf(delta, u.a[q], u.s[q].z * fmaf(lambda, u.s[q].x, u.s[q].y));
+                float4 *ptr = P.state + u.c[q] * stride;
+                const float4 cur = ld_state(ptr);
+                __stcg(reinterpret_cast<float2 *>(ptr), make_float2(cur.x + dx, cur.y + delta * u.a[q] * inv_n));
+            }
+        }
+        if (lane == 0) __stcg(P.alpha + u.i, __ldcg(P.alpha + u.i) + delta);
+        return;
+    }
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
         if (lane + 32 * q < u.len) {
@@ -237,18 +251,19 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
         __syncwarp();
         const int m = (int)(k & (kMetaRing - 1));
         if (R.row[m] < 0) break;
-        uint64_t t_read = 0;
-        if (P.trace) t_read = globaltimer_ns();
-        Update<kDense> u;
-        const bool ok = begin_update<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u);
-        // while the reads are in flight: stage the slice of row k + 2 and the row_ptr entries of row k + 4
+        // stage the slice of row k + 2 and the row_ptr entries of row k + 4 before
+        // touching the state: the window between this update's reads and
+        // writes (which sets the overlap tau) then holds no staging work
         const int m2 = (int)((k + 2) & (kMetaRing - 1));
         stage_slice<T, kDense>(P, R, m2, (int)((k + 2) & (kStages - 1)), lane);
         const bool more = R.row[(k + 3) & (kMetaRing - 1)] >= 0;
         stage_meta<kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
                            lane);
         cp_async_commit();
-        if (ok) finish_update<T, kDense>(P, u, lane);
+        uint64_t t_read = 0;
+        if (P.trace) t_read = globaltimer_ns();
+        Update<kDense> u;
+        if (begin_update<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u)) finish_update<T, kDense>(P, u, lane);
         if (P.trace && lane == 0) {
             P.trace[2 * (warp + k * W)] = t_read;
             P.trace[2 * (warp + k * W) + 1] = globaltimer_ns();

@@ -329,3 +329,17 @@ def test_overlap_is_zero_for_one_warp_and_grows_with_warps():
         assert 0.3 * 255 <= o["tau_mean"] <= 3 * 256, o
         assert o["tau_paper"] >= o["tau_mean"] and o["tau_max"] >= o["tau_paper"]
         assert o["window_ns_mean"] > 0
+
+
+def test_plain_writes_break_the_average_invariant():
+    """App. G.2: without atomic adds, concurrent updates are lost, so abar no
+    longer equals (1/n) sum_i alpha_i a_i (the bookkeeping behind the floor the
+    paper observes); with atomic adds the gap is float32 rounding."""
+    p = synth.rcv1_like(seed=31, n=60000, d=6000)
+    drift = {}
+    for plain in (0, 1):
+        with asaga.Context(p, seed=4, max_warps=1024, gamma=0.05, plain_writes=plain) as c:
+            asaga.asaga_run(c.ctx, 3)
+            drift[plain] = asaga.asaga_recompute_abar(c.ctx)
+    assert drift[0] < 1e-5
+    assert drift[1] > 30 * drift[0]
