@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--experiment", default=None, choices=["warps", "overlap", "cas"],
+                    help="reproduce one of the paper's qualitative experiments instead of the benchmark")
     ap.add_argument("--warps", type=int, default=0, help="fixed concurrent warps (skips the autotuner)")
     ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
     return ap.parse_args()
@@ -339,8 +341,64 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def run_experiment(args):
+    """The paper's qualitative experiments on the GPU, one JSON line each:
+      warps   -- epochs (and device seconds) to 1e-6 against the number of concurrent
+                 warps, each at its fastest stable step (App. D.2, "theoretical speedups");
+      overlap -- the overlap tau against the number of warps (App. E.2);
+      cas     -- atomic against non-thread-safe updates: suboptimality reached and
+                 the abar bookkeeping error (App. G.2)."""
+    import torch
+    from paper_1606_04809_gb300 import asaga
+    from paper_1606_04809_gb300 import build as lib_build
+
+    lib_build.build()
+    asaga.load()
+    wl = WORKLOADS[args.workload]
+    p = wl["make"]()
+    storage = p.storage if p.storage != "f64" else "f32"
+    golden, why = load_golden(wl["golden"], p)
+    if golden is None:
+        raise SystemExit(why)
+    fstar = golden["fstar"]
+    out = {"experiment": args.experiment, "workload": wl["desc"], "fstar": fstar}
+    rows = []
+    if args.experiment == "warps":
+        with asaga.Context(p, storage=storage) as c:
+            gamma0 = asaga.asaga_get_info(c.ctx)["gamma"]
+        for W in (16, 64, 256, 512, 1024, 2048):
+            best = {"warps": W, "epochs": None}
+            for k in range(0, 9):  # steps gamma0 * 2^(-k/2), largest first: keep the first that converges
+                with asaga.Context(p, storage=storage, seed=7, max_warps=W, gamma=gamma0 * 2 ** (-k / 2),
+                                   abar_recompute_every=ABAR_EVERY) as c:
+                    s, r = asaga.asaga_run(c.ctx, 60, TARGET, fstar)
+                if s == asaga.OK:
+                    best = {"warps": W, "gamma_scale": 2 ** (-k / 2), "epochs": r.epochs,
+                            "seconds_device": r.solver_seconds + r.eval_seconds}
+                    break
+            rows.append(best)
+    elif args.experiment == "overlap":
+        for W in (1, 16, 64, 256, 512, 1024, 2048, 4096):
+            with asaga.Context(p, storage=storage, seed=7, max_warps=W, gamma=0.01) as c:
+                o = asaga.asaga_measure_overlap(c.ctx, 0.05 if W == 1 else 1.0)
+            rows.append(o)
+    else:  # cas
+        for plain in (0, 1):
+            with asaga.Context(p, storage=storage, seed=7, max_warps=1024, gamma=0.05, plain_writes=plain,
+                               abar_recompute_every=0) as c:
+                s, r = asaga.asaga_run(c.ctx, 30, 0.0, fstar)
+                drift = asaga.asaga_recompute_abar(c.ctx)
+                f = asaga.asaga_objective(c.ctx)
+            rows.append({"plain_writes": plain, "epochs": r.epochs, "rel_subopt": (f - fstar) / abs(fstar),
+                         "abar_error": drift})
+    out["rows"] = rows
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.experiment:
+        return run_experiment(args)
     if args.workload == "batch":
         return run_batch(args)
     world, rank, local = dist_env()
