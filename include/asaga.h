@@ -157,7 +157,7 @@ typedef struct {
 typedef struct {
     int warps;           /* chosen number of concurrent solver warps            */
     double gamma;        /* chosen step size                                    */
-    double score;        /* ln(1e6) / device seconds of the winning trial        */
+    double score;        /* ln(1e4) / device seconds of the winning trial        */
     int trials;          /* (warps, gamma) pairs tried                          */
     double seconds;      /* device time spent in the trials                      */
 } asaga_tune_result;
@@ -191,21 +191,23 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
 /* Picks the number of concurrent warps and the step size for asaga_run.
  * The overlap tau of asynchronous updates grows with the number of warps,
  * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)),
- * so the fastest schedule is found by measurement.  Each trial starts from
- * x = 0, alpha = 0 and runs epochs with one (warps, gamma) pair until the
- * float64 |grad f|^2 has shrunk by 1e-6 (or diverges, or reaches
- * trial_epochs epochs (<= 0: 40), or is already 1.5x slower than the best
- * trial).  Warp counts go from the resident maximum (at most n/4) down by
- * halves to 4; for each, steps gamma0 * 2^(-k/2), k = -4..12 (gamma0 =
- * options.gamma or 1/(3L); the paper's own grid reaches 10/L), are tried
- * from large to small until the time stops improving -- starting at gamma0
- * for the largest warp count and two notches above the previous winner for
- * each smaller one (fewer warps overlap less, so larger steps can be stable).
- * The pair with the least update-kernel time wins; the step used is one
- * notch (1/sqrt 2) below the winning one, a margin for run-to-run variation
- * of asynchronous execution.  score = ln(1e6) / (winning time in seconds).
- * Leaves the state at x = 0, alpha = 0, abar = 0 (sampler position 0) with
- * the chosen pair in use.  EINVAL in deterministic mode. */
+ * so the fastest schedule is found by measurement, in two stages, each trial
+ * starting from x = 0, alpha = 0:
+ *  1. at 256 warps (at most n/4), steps gamma0 * 2^(-k/2) (gamma0 =
+ *     options.gamma or 1/(3L); k = -4, -3, ...) are tried from large to
+ *     small in 6-epoch trials until one is stable (the float64 |grad f|^2
+ *     falls monotonically over the last two epochs and ends below half its
+ *     start); warps x step is taken as the stability frontier;
+ *  2. warp counts (powers of 2 from 4 to the resident maximum, at most n/4),
+ *     each at the frontier step (snapped to the ladder), race until
+ *     |grad f|^2 has shrunk by 1e-4 (at most trial_epochs epochs, <= 0: 30),
+ *     starting where the step is ~0.4 gamma0 and moving outwards while the
+ *     time improves; a diverging candidate gets one notch smaller a step.
+ * The fastest candidate wins; its step is used one notch (1/sqrt 2) lower,
+ * a margin for run-to-run variation of asynchronous execution.
+ * score = ln(1e4) / (winning time in seconds).  Leaves the state at x = 0,
+ * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
+ * EINVAL in deterministic mode. */
 asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);
 
 /* Overlap of the asynchronous updates (the tau of Assumption 1). */

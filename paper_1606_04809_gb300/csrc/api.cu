@@ -717,22 +717,39 @@ asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, double red
     return ASAGA_OK;
 }
 
+// Short stability trial: E epochs from x = 0; stable when |grad f|^2 fell
+// monotonically over the last two epochs and ended below half its start.
+asaga_status stability_trial(asaga_ctx *c, int W, double gamma, double g0, int E, bool *stable, double *t_ms,
+                             std::string *err) {
+    TRY(reset_state(c, err));
+    double g[3] = {g0, g0, g0};
+    *t_ms = 0;
+    *stable = false;
+    double g_min = g0;
+    for (int e = 1; e <= E; ++e) {
+        double ms = 0, g2 = 0;
+        const bool want = e >= E - 2 || e % 2 == 0;
+        TRY(trial_epoch(c, W, gamma, &ms, want ? &g2 : nullptr, err));
+        *t_ms += ms;
+        if (want) {
+            if (!std::isfinite(g2) || g2 > 4.0 * g_min) return ASAGA_OK;  // diverging
+            g_min = std::min(g_min, g2);
+            if (e >= E - 2) g[e - (E - 2)] = g2;
+        }
+    }
+    *stable = g[2] <= g[1] && g[1] <= g[0] && g[2] < 0.5 * g0;
+    return ASAGA_OK;
+}
+
 asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 40;
-    const double reduction = 1e-6;  // trials race to shrink |grad f|^2 by this factor
-    // warp counts, largest first: the resident maximum (at most n/4), then halvings down to 32
-    std::vector<int> cands;
+    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 30;
+    const double reduction = 1e-4;  // candidates race to shrink |grad f|^2 by this factor
     const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
-    cands.push_back((int)cap);
-    int64_t w = 1;
-    while (w * 2 < cap) w *= 2;
-    for (; w >= 4; w /= 2)
-        if (w < cap) cands.push_back((int)w);
-    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2), from 4 gamma0 down to gamma0/64
-    for (int k = -4; k <= 12; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
+    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2), k = -4..16
+    for (int k = -4; k <= 16; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -743,40 +760,77 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
     TRY(stream_sync(c, err));
     const double g0 = c->hout[2];
+
+    // 1. the stability frontier: largest stable step at a probe warp count
+    const int Wp = (int)std::min<int64_t>(cap, 256);
+    double frontier = 0;  // warps x scale
+    for (size_t k = 0; k < scales.size(); ++k) {
+        bool stable = false;
+        double t_ms = 0;
+        TRY(stability_trial(c, Wp, c->gamma_base * scales[k], g0, 6, &stable, &t_ms, err));
+        ++r.trials;
+        r.seconds += t_ms * 1e-3;
+        if (stable) {
+            frontier = Wp * scales[k];
+            break;
+        }
+    }
+    if (frontier <= 0) {  // nothing stable even at the smallest step: keep the defaults
+        TRY(reset_state(c, err));
+        if (res) *res = r;
+        return ASAGA_OK;
+    }
+    // 2. race warp counts along the frontier (step = frontier / warps, snapped down
+    //    to the ladder), starting where the step reaches ~0.4 gamma0, outwards
+    auto snap = [&](double want) -> long {
+        for (size_t k = 0; k < scales.size(); ++k)
+            if (scales[k] <= want * (1 + 1e-12)) return (long)k;
+        return -1;
+    };
+    std::vector<int> pow2;
+    for (int64_t w = 4; w <= cap; w *= 2) pow2.push_back((int)w);
+    if (pow2.empty() || pow2.back() != cap) pow2.push_back((int)cap);
+    const double w_star = frontier / 0.4;
+    int centre = 0;
+    for (int j = 0; j < (int)pow2.size(); ++j)
+        if (std::fabs(std::log((double)pow2[j] / w_star)) < std::fabs(std::log((double)pow2[centre] / w_star))) centre = j;
     double best_ms = INFINITY;
-    size_t best_k = 0;
-    size_t first_k = 4;  // the first (largest) warp count starts at gamma0 itself
-    for (int W : cands) {
-        double w_best = INFINITY;
-        long w_k = -1;
-        for (size_t k = first_k; k < scales.size(); ++k) {
+    long best_k = -1;
+    auto try_w = [&](int W) -> asaga_status {
+        long k = snap(frontier / W);
+        if (k < 0) return ASAGA_OK;
+        for (int attempt = 0; attempt < 2 && k < (long)scales.size(); ++attempt, ++k) {
             bool ok = false;
             double t_ms = 0;
             int ep = 0;
             const double give_up = std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY;
-            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep,
-                           err));
+            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep, err));
             ++r.trials;
             r.seconds += t_ms * 1e-3;
-            if (ok && t_ms < w_best) {
-                w_best = t_ms;
-                w_k = (long)k;
-            } else if (w_k >= 0) {
-                break;  // smaller steps only get slower from here
+            if (ok) {
+                if (t_ms < best_ms) {
+                    best_ms = t_ms;
+                    best_k = k;
+                    r.warps = W;
+                }
+                return ASAGA_OK;
             }
+            if (t_ms > give_up) return ASAGA_OK;  // slower than the best so far: do not back off further
         }
-        if (w_k < 0) continue;  // nothing converged at this warp count: try fewer warps
-        if (w_best < best_ms) {
-            best_ms = w_best;
-            best_k = (size_t)w_k;
-            r.warps = W;
-        } else if (w_best > 1.5 * best_ms) {
-            break;  // past the best warp count
-        }
-        // half the warps roughly halves the overlap: larger steps become stable
-        first_k = w_k >= 2 ? (size_t)w_k - 2 : 0;
+        return ASAGA_OK;
+    };
+    TRY(try_w(pow2[centre]));
+    for (int j = centre + 1; j < (int)pow2.size(); ++j) {  // more warps, smaller steps
+        const double before = best_ms;
+        TRY(try_w(pow2[j]));
+        if (!(best_ms < before)) break;
     }
-    if (std::isfinite(best_ms)) {
+    for (int j = centre - 1; j >= 0; --j) {  // fewer warps, larger steps
+        const double before = best_ms;
+        TRY(try_w(pow2[j]));
+        if (!(best_ms < before)) break;
+    }
+    if (best_k >= 0) {
         // one notch below the fastest step: asynchronous runs vary from run to run
         r.gamma = c->gamma_base * scales[best_k] * std::sqrt(0.5);
         r.score = std::log(1.0 / reduction) / (best_ms * 1e-3);
