@@ -157,7 +157,7 @@ typedef struct {
 typedef struct {
     int warps;           /* chosen number of concurrent solver warps            */
     double gamma;        /* chosen step size                                    */
-    double score;        /* ln(1e4) / device seconds of the winning trial        */
+    double score;        /* ln(1e6) / device seconds of the winning trial        */
     int trials;          /* (warps, gamma) pairs tried                          */
     double seconds;      /* device time spent in the trials                      */
 } asaga_tune_result;
@@ -200,12 +200,13 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  *     start); warps x step is taken as the stability frontier;
  *  2. warp counts (powers of 2 from 4 to the resident maximum, at most n/4),
  *     each at the frontier step (snapped to the ladder), race until
- *     |grad f|^2 has shrunk by 1e-4 (at most trial_epochs epochs, <= 0: 30),
+ *     |grad f|^2 has shrunk by 1e-6 (at most trial_epochs epochs, <= 0: 40),
  *     starting where the step is ~0.4 gamma0 and moving outwards while the
  *     time improves; a diverging candidate gets one notch smaller a step.
- * The fastest candidate wins; its step is used one notch (1/sqrt 2) lower,
+ * The fastest candidate wins (if none reaches the reduction, the one whose
+ * |grad f|^2 fell fastest, monotonically, does); its step is used one notch (1/sqrt 2) lower,
  * a margin for run-to-run variation of asynchronous execution.
- * score = ln(1e4) / (winning time in seconds).  Leaves the state at x = 0,
+ * score = ln(1e6) / (winning time in seconds).  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
  * EINVAL in deterministic mode. */
 asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);

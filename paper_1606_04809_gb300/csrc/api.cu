@@ -695,12 +695,15 @@ asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, doub
 // |grad f|^2 <= reduction * |grad f(0)|^2 (success), divergence, max_epochs,
 // or more update-kernel time than `give_up_ms`.  Returns the kernel time.
 asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, double reduction, int max_epochs,
-                        double give_up_ms, bool *success, double *t_ms, int *epochs, std::string *err) {
+                        double give_up_ms, bool *success, double *t_ms, int *epochs, std::string *err,
+                        double *rate = nullptr) {
     TRY(reset_state(c, err));
     *success = false;
     *t_ms = 0;
     *epochs = 0;
-    double g_min = g0;
+    if (rate) *rate = -1.0;
+    double g_min = g0, g_prev = g0;
+    bool monotone = true;
     for (int e = 1; e <= max_epochs; ++e) {
         double ms = 0, g = 0;
         TRY(trial_epoch(c, W, gamma, &ms, &g, err));
@@ -708,6 +711,10 @@ asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, double red
         *epochs = e;
         if (!std::isfinite(g) || (e >= 3 && g > 4.0 * g_min)) return ASAGA_OK;  // diverging
         g_min = std::min(g_min, g);
+        if (e >= max_epochs - 2 && g > g_prev) monotone = false;
+        g_prev = g;
+        // decrease of ln |grad f|^2 per second so far (used when no trial reaches the reduction)
+        if (rate && monotone && g < g0) *rate = std::log(g0 / g) / (*t_ms * 1e-3);
         if (g <= reduction * g0) {
             *success = true;
             return ASAGA_OK;
@@ -745,8 +752,8 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 30;
-    const double reduction = 1e-4;  // candidates race to shrink |grad f|^2 by this factor
+    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 40;
+    const double reduction = 1e-6;  // candidates race to shrink |grad f|^2 by this factor
     const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
     std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2), k = -4..16
     for (int k = -4; k <= 16; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
@@ -796,6 +803,9 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         if (std::fabs(std::log((double)pow2[j] / w_star)) < std::fabs(std::log((double)pow2[centre] / w_star))) centre = j;
     double best_ms = INFINITY;
     long best_k = -1;
+    double best_rate = -1.0;  // fallback when no candidate reaches the reduction
+    long rate_k = -1;
+    int rate_w = 0;
     auto try_w = [&](int W) -> asaga_status {
         long k = snap(frontier / W);
         if (k < 0) return ASAGA_OK;
@@ -804,9 +814,16 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
             double t_ms = 0;
             int ep = 0;
             const double give_up = std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY;
-            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep, err));
+            double rate = -1.0;
+            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep, err,
+                           &rate));
             ++r.trials;
             r.seconds += t_ms * 1e-3;
+            if (!ok && rate > best_rate) {
+                best_rate = rate;
+                rate_k = k;
+                rate_w = W;
+            }
             if (ok) {
                 if (t_ms < best_ms) {
                     best_ms = t_ms;
@@ -829,6 +846,11 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         const double before = best_ms;
         TRY(try_w(pow2[j]));
         if (!(best_ms < before)) break;
+    }
+    if (best_k < 0 && rate_k >= 0) {  // slow problems: no candidate reached the reduction in time
+        best_k = rate_k;
+        r.warps = rate_w;
+        best_ms = std::log(1.0 / reduction) / best_rate * 1e3;
     }
     if (best_k >= 0) {
         // one notch below the fastest step: asynchronous runs vary from run to run
