@@ -53,6 +53,9 @@ typedef enum { ASAGA_LOSS_LOGISTIC = 0, ASAGA_LOSS_SQUARED = 1 } asaga_loss;
 
 typedef enum { ASAGA_F64 = 0, ASAGA_F32 = 1, ASAGA_BF16 = 2, ASAGA_F16 = 3 } asaga_dtype;
 
+/* Row sampling of the asynchronous updates (asaga_options.sampling). */
+typedef enum { ASAGA_SAMPLE_UNIFORM = 0, ASAGA_SAMPLE_PERMUTATION = 1 } asaga_sampling;
+
 /*
  * The data matrix A (n rows a_i, d columns) in CSR form, and the labels.
  *   row_ptr  int64[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz;
@@ -105,6 +108,11 @@ typedef struct {
  *                        load-add-store updates, which lose concurrent adds:
  *                        the comparison of App. G.2 ("Necessity of
  *                        compare-and-swap"), for diagnostics only; 0 = atomic.
+ *   sampling             ASAGA_SAMPLE_UNIFORM (default): rows drawn uniformly
+ *                        with replacement, as Algorithm 2 does;
+ *                        ASAGA_SAMPLE_PERMUTATION: every epoch visits each row
+ *                        once, in a seeded pseudo-random order (a variant
+ *                        the paper does not analyse; see asaga_sample_rows).
  */
 typedef struct {
     asaga_loss loss;
@@ -120,6 +128,7 @@ typedef struct {
     void *cuda_stream;
     int column_stride;
     int plain_writes;
+    int sampling;
 } asaga_options;
 
 /* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and
@@ -157,7 +166,7 @@ typedef struct {
 typedef struct {
     int warps;           /* chosen number of concurrent solver warps            */
     double gamma;        /* chosen step size                                    */
-    double score;        /* ln(1e6) / device seconds of the winning trial        */
+    double score;        /* higher is better; -1 when no trial settled          */
     int trials;          /* (warps, gamma) pairs tried                          */
     double seconds;      /* device time spent in the trials                      */
 } asaga_tune_result;
@@ -190,26 +199,51 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
 
 /* Picks the number of concurrent warps and the step size for asaga_run.
  * The overlap tau of asynchronous updates grows with the number of warps,
- * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)),
- * so the fastest schedule is found by measurement, in two stages, each trial
- * starting from x = 0, alpha = 0:
- *  1. at 256 warps (at most n/4), steps gamma0 * 2^(-k/2) (gamma0 =
- *     options.gamma or 1/(3L); k = -4, -3, ...) are tried from large to
- *     small in 6-epoch trials until one is stable (the float64 |grad f|^2
- *     falls monotonically over the last two epochs and ends below half its
- *     start); warps x step is taken as the stability frontier;
- *  2. warp counts (powers of 2 from 4 to the resident maximum, at most n/4),
- *     each at the frontier step (snapped to the ladder), race until
- *     |grad f|^2 has shrunk by 1e-6 (at most trial_epochs epochs, <= 0: 40),
- *     starting where the step is ~0.4 gamma0 and moving outwards while the
- *     time improves; a diverging candidate gets one notch smaller a step.
- * The fastest candidate wins (if none reaches the reduction, the one whose
- * |grad f|^2 fell fastest, monotonically, does); its step is used one notch (1/sqrt 2) lower,
- * a margin for run-to-run variation of asynchronous execution.
- * score = ln(1e6) / (winning time in seconds).  Leaves the state at x = 0,
+ * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)).
+ * Measured on a GB300: warps x step has a stability frontier, above which
+ * the iterate stalls on a plateau (logistic loss) or diverges (squared loss);
+ * below it the epochs needed depend on the step only, while the epoch time
+ * falls with the number of warps.  Steps are gamma0 * 2^(-k/2), gamma0 =
+ * options.gamma or 1/(3L), k = -4..16.  Each trial starts from x = 0,
+ * alpha = 0 and records the float64 |grad f|^2 after every epoch:
+ *  1. frontier: at min(1024, n/4, resident) warps, bisection over k for the
+ *     largest step whose 16-epoch trial converges (|grad f|^2 shrinks by
+ *     1e6, or its log falls with a least-squares t-statistic >= 3.5);
+ *     if none does, again with 8x fewer warps (twice at most);
+ *  2. race: warp counts W = probe * 2^j at one notch inside the frontier
+ *     (W x step constant), scored by the predicted update time for
+ *     |grad f|^2 to shrink by 1e10 (the least-squares trend of the trial's
+ *     last two thirds, if its t-statistic is >= 3); trials run trial_epochs
+ *     epochs (<= 0: 24) and stop when slower than 1.5x the best so far;
+ *  3. smaller steps at the winning warp count while they score better.
+ * If no trial converges, the defaults stay.  score = 1 / (predicted
+ * seconds of the winner), -1 when none settled.  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
  * EINVAL in deterministic mode. */
 asaga_status asaga_autotune(asaga_ctx *ctx, double trial_epochs, asaga_tune_result *res);
+
+/* The rows that updates t_begin .. t_begin+count-1 of a context with this
+ * seed, n and sampling visit, computed by the solver's own device sampler
+ * (the same function the update kernel calls) and written to rows[count]
+ * (host memory).  A context numbers its updates from 0 (after asaga_create
+ * and asaga_autotune; asaga_set_state sets the count).
+ *  - ASAGA_SAMPLE_UNIFORM (Algorithm 2 samples i uniformly, with
+ *    replacement): u_t = the (t+1)-th output of SplitMix64 (Steele, Lea and
+ *    Flood, OOPSLA 2014) seeded with `seed`, row = floor(u_t n / 2^64).
+ *  - ASAGA_SAMPLE_PERMUTATION: epoch e = floor(t / n) visits position
+ *    p = t - e n at row pi_e(p), where pi_e is a bijection of [0, n): a
+ *    4-round balanced Feistel network on 2h bits (h >= 1 the smallest with
+ *    4^h >= n; left half = high h bits), round r = 0..3 mapping
+ *    (L, R) -> (R, L xor (M((k_e xor R) + (r+1) G) mod 2^h)), iterated until
+ *    the value falls below n (cycle walking).  G = 0x9E3779B97F4A7C15, M is
+ *    SplitMix64's output mix, k_e = the (e+1)-th output of SplitMix64 seeded
+ *    with seed xor 0xD1B54A32D192ED03.
+ * EINVAL: n < 1 (or n > 2^62 with permutation sampling), count < 0, rows
+ * NULL with count > 0, unknown sampling.  ECUDA / ENOMEM: no usable GPU.
+ * The paper has no counterpart of this call; it exposes the sampler for
+ * checking and for replaying a run's row sequence. */
+asaga_status asaga_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
+                               int64_t *rows);
 
 /* Overlap of the asynchronous updates (the tau of Assumption 1). */
 typedef struct {
@@ -267,8 +301,9 @@ asaga_status asaga_set_state(asaga_ctx *ctx, const float *x, const float *abar,
 
 asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
 
-/* Reason for the last failure of a call on ctx (or of asaga_create when ctx
- * is NULL); never NULL. */
+/* Reason for the last failure of a call on ctx (or, when ctx is NULL, of
+ * the calling thread's last asaga_create, asaga_sample_rows or
+ * asaga_recompute_abar_noalloc); never NULL. */
 const char *asaga_last_error(const asaga_ctx *ctx);
 
 const char *asaga_status_string(asaga_status s);
@@ -309,10 +344,13 @@ asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, c
 
 /* Per-instance step sizes from shared trials: the schedule is reset to the
  * default, and every trial runs all instances at once for trial_epochs
- * epochs (<= 0: 8) from x = 0 with gamma_i = s * gamma0_i, s on the ladder
- * 2^(-k/2), k = -4..8; each instance keeps the s under which its float64 |grad f_i|^2
- * fell most (decreasing over the last two epochs), one notch lower as a
- * margin.  Leaves every instance at x = 0.  results[i] may be NULL. */
+ * epochs (<= 0: 16) from x = 0 with gamma_i = s * gamma0_i, s = 2^(-k/2) on
+ * the ladder k = -4..12 (stopping once smaller steps help no instance),
+ * recording each float64 |grad f_i|^2 after every epoch.  Each instance
+ * takes the largest step that converges (the test of asaga_autotune), and
+ * then, from one notch inside it on, the step with the fewest predicted
+ * epochs (the trend test of asaga_autotune).  Leaves every instance at
+ * x = 0.  results[i] may be NULL; its score is 1 / predicted epochs. */
 asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);
 
 /* Overrides the schedule: warps[i] (rounded up to a multiple of 4) and/or

@@ -12,6 +12,10 @@ for a reader to check by eye against the paper:
   term (Eq. SparseSAGA and Sec. 4.2), run by the C file ``saga_ref.c``;
 * ``dense_saga_step`` -- the original SAGA update (Eq. SAGAupdate), used only
   to check the sparse variant against it;
+* ``lagged_saga`` -- the same dense SAGA iteration with lagged updates
+  (App. C), the serial baseline the paper compares Sparse SAGA with;
+* ``splitmix64`` / ``sampler_indices`` -- the published SplitMix64 generator
+  and the row sampling built on it, written independently of the solver's;
 * ``newton`` / ``ridge_closed_form`` -- exact minimisers used to certify f*.
 
 Only ``tests/``, the smoke check and the benchmark's CPU-baseline leg may use
@@ -47,6 +51,11 @@ def lib():
         L.oracle_sparse_saga.restype = i32
         L.oracle_row_derivatives.argtypes = [i64, dp, dp, dp, dp, i32, dp, dp]
         L.oracle_row_derivatives.restype = None
+        L.oracle_lagged_saga.argtypes = [i64, i64, dp, dp, dp, dp, i32, ctypes.c_double,
+                                         ctypes.c_double, dp, dp, dp, dp, dp, i64, i64]
+        L.oracle_lagged_saga.restype = i32
+        L.oracle_lagged_catch_up.argtypes = [i64, ctypes.c_double, ctypes.c_double, dp, dp, dp, i64]
+        L.oracle_lagged_catch_up.restype = None
         _lib = L
     return _lib
 
@@ -190,6 +199,68 @@ def sparse_saga(p, state: State, idx: np.ndarray, gamma: float, D: Optional[np.n
     if rc != 0:
         raise ValueError("index out of range")
     return state
+
+
+def lagged_saga(p, state: State, idx: np.ndarray, gamma: float) -> State:
+    """Runs len(idx) steps of dense SAGA (Eq. SAGAupdate) in place with the
+    lagged-update scheme of App. C (C file ``saga_ref.c``): per step only the
+    sampled support is touched, the other coordinates catch up in closed
+    form when next read, and all of them at the end.  For comparison with
+    Sparse SAGA only; the solver has no counterpart."""
+    rp = np.ascontiguousarray(p.row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(p.col_idx, dtype=np.int32)
+    va = np.ascontiguousarray(p.values, dtype=np.float64)
+    lb = np.ascontiguousarray(p.labels, dtype=np.float64)
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    last = np.zeros(p.d, dtype=np.int64)
+    for a in (state.x, state.alpha, state.abar):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    L = lib()
+    rc = L.oracle_lagged_saga(p.n, p.d, _ptr(rp), _ptr(ci), _ptr(va), _ptr(lb), LOSS_CODES[p.loss],
+                              float(p.lam), float(gamma), _ptr(state.x), _ptr(state.alpha),
+                              _ptr(state.abar), _ptr(last), _ptr(ix), ix.size, 0)
+    if rc != 0:
+        raise ValueError("index out of range")
+    L.oracle_lagged_catch_up(p.d, float(p.lam), float(gamma), _ptr(state.x), _ptr(state.abar),
+                             _ptr(last), ix.size)
+    return state
+
+
+# --------------------------------------------------------------------------
+# row sampling: Algorithm 2 draws i uniformly (with replacement) before it
+# reads anything.  The stream is the published SplitMix64 generator (Steele,
+# Lea and Flood, "Fast splittable pseudorandom number generators", OOPSLA
+# 2014); update t takes the generator's (t+1)-th output u_t for a given seed
+# and the row floor(u_t n / 2^64).
+# --------------------------------------------------------------------------
+_SPLITMIX_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(seed: int, count: int) -> list:
+    """The first `count` outputs of SplitMix64 seeded with `seed` (plain
+    Python integers, one step at a time)."""
+    out, state = [], seed & _M64
+    for _ in range(count):
+        state = (state + _SPLITMIX_GAMMA) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        out.append(z ^ (z >> 31))
+    return out
+
+
+def sampler_indices(seed: int, n: int, t_begin: int, count: int) -> np.ndarray:
+    """Rows of updates t_begin .. t_begin+count-1 (int64), computed with exact
+    integer arithmetic per update."""
+    rows = np.empty(count, dtype=np.int64)
+    for j in range(count):
+        state = (seed + (t_begin + j + 1) * _SPLITMIX_GAMMA) & _M64
+        z = state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+        rows[j] = ((z ^ (z >> 31)) * n) >> 64
+    return rows
 
 
 def row_derivatives(p, x: np.ndarray) -> np.ndarray:

@@ -101,3 +101,75 @@ void oracle_row_derivatives(int64_t n, const int64_t *row_ptr, const int32_t *co
         out[i] = phi_prime(loss, z, labels[i]);
     }
 }
+
+/*
+ * Serial SAGA with lagged updates (App. C.1 and C.2, the "just-in-time"
+ * scheme of the SAG/SAGA literature that the paper compares Sparse SAGA with).
+ * It computes the dense SAGA iteration (Eq. SAGAupdate with the l2 term's
+ * gradient lambda x taken exactly):
+ *     x+ = x - gamma (delta a_i + abar + lambda x),  delta = phi'_i - alpha_i,
+ * but touches only S_i per step.  A coordinate v outside S_i receives
+ * x_v <- (1 - gamma lambda) x_v - gamma abar_v, and abar_v cannot change
+ * until v is in a sampled support again, so those steps are deferred and
+ * applied in closed form when v is next read:
+ *     m steps:  x_v <- c^m x_v - gamma abar_v (1 + c + ... + c^(m-1)),
+ *     c = 1 - gamma lambda,  the sum = (1 - c^m) / (gamma lambda)  (m if lambda = 0).
+ * last[v] is the number of steps already applied to x_v.  In exact
+ * arithmetic the iterate equals dense SAGA's after oracle_lagged_catch_up.
+ * Returns 0, or -1 on an out-of-range index.  Steps are numbered t0 .. t0+T-1.
+ */
+static double lagged_x(double xv, double abar_v, double gamma, double lambda, int64_t m)
+{
+    if (m <= 0)
+        return xv;
+    if (lambda == 0.0)
+        return xv - gamma * abar_v * (double)m;
+    double log_c = log1p(-gamma * lambda);
+    double cm = exp((double)m * log_c);
+    double one_minus_cm = -expm1((double)m * log_c);
+    return cm * xv - abar_v * one_minus_cm / lambda;
+}
+
+int oracle_lagged_saga(int64_t n, int64_t d, const int64_t *row_ptr, const int32_t *col_idx,
+                       const double *val, const double *labels, int loss, double lambda,
+                       double gamma, double *x, double *alpha, double *abar, int64_t *last,
+                       const int64_t *idx, int64_t T, int64_t t0)
+{
+    for (int64_t s = 0; s < T; ++s) {
+        int64_t t = t0 + s;
+        int64_t i = idx[s];
+        if (i < 0 || i >= n)
+            return -1;
+        int64_t lo = row_ptr[i], hi = row_ptr[i + 1];
+        double z = 0.0;
+        for (int64_t k = lo; k < hi; ++k) {
+            int32_t v = col_idx[k];
+            if (v < 0 || v >= d)
+                return -1;
+            x[v] = lagged_x(x[v], abar[v], gamma, lambda, t - last[v]);
+            last[v] = t;
+            z += val[k] * x[v];
+        }
+        double g = phi_prime(loss, z, labels[i]);
+        double delta = g - alpha[i];
+        for (int64_t k = lo; k < hi; ++k) {
+            int32_t v = col_idx[k];
+            double a = val[k];
+            x[v] -= gamma * (delta * a + abar[v] + lambda * x[v]);
+            last[v] = t + 1;
+            abar[v] += delta * a / (double)n;
+        }
+        alpha[i] = g;
+    }
+    return 0;
+}
+
+/* Applies every deferred step up to step t_end (the end of a run). */
+void oracle_lagged_catch_up(int64_t d, double lambda, double gamma, double *x, const double *abar,
+                            int64_t *last, int64_t t_end)
+{
+    for (int64_t v = 0; v < d; ++v) {
+        x[v] = lagged_x(x[v], abar[v], gamma, lambda, t_end - last[v]);
+        last[v] = t_end;
+    }
+}

@@ -26,6 +26,7 @@ STATUS_NAMES = ["ASAGA_OK", "ASAGA_EINVAL", "ASAGA_ENOMEM", "ASAGA_ECUDA", "ASAG
                 "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED"]
 LOSS = {"logistic": 0, "squared": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+SAMPLING = {"uniform": 0, "permutation": 1}
 
 
 class AsagaError(RuntimeError):
@@ -48,7 +49,7 @@ class asaga_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("epochs_per_segment", ctypes.c_int),
                 ("abar_recompute_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int),
-                ("plain_writes", ctypes.c_int)]
+                ("plain_writes", ctypes.c_int), ("sampling", ctypes.c_int)]
 
 
 class asaga_result(ctypes.Structure):
@@ -127,6 +128,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_status_string.restype = ctypes.c_char_p
     L.asaga_recompute_abar_noalloc.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
     L.asaga_recompute_abar_noalloc.restype = i32
+    L.asaga_sample_rows.argtypes = [ctypes.c_uint64, i64, i32, ctypes.c_uint64, i64, vp]
+    L.asaga_sample_rows.restype = i32
     L.asaga_destroy.argtypes = [vp]
     L.asaga_destroy.restype = None
     L.asaga_batch_create.argtypes = [P(vp), i32, P(asaga_problem), P(asaga_options)]
@@ -181,6 +184,8 @@ def asaga_default_options(**overrides) -> asaga_options:
             v = LOSS[v]
         if k == "storage_dtype" and isinstance(v, str):
             v = DTYPE[v]
+        if k == "sampling" and isinstance(v, str):
+            v = SAMPLING[v]
         if not hasattr(o, k):
             raise AttributeError(k)
         setattr(o, k, v)
@@ -282,6 +287,15 @@ def asaga_recompute_abar_noalloc(n, d, row_ptr, col_idx, values, alpha, abar, dr
     s = load().asaga_recompute_abar_noalloc(int(n), int(d), _ptr(row_ptr), _ptr(col_idx), _ptr(values),
                                             _ptr(alpha), _ptr(abar), _ptr(drift), stream)
     _check(None, s)
+
+
+def asaga_sample_rows(seed: int, n: int, t_begin: int, count: int, sampling="uniform") -> np.ndarray:
+    """Rows of updates t_begin .. t_begin+count-1 from the device sampler (int64)."""
+    rows = np.empty(max(int(count), 0), dtype=np.int64)
+    smp = SAMPLING[sampling] if isinstance(sampling, str) else int(sampling)
+    s = load().asaga_sample_rows(int(seed), int(n), smp, int(t_begin), int(count), _ptr(rows) if count else None)
+    _check(None, s)
+    return rows
 
 
 def asaga_get_state(ctx: int):

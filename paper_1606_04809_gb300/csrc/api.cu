@@ -35,6 +35,7 @@ struct asaga_ctx {
     double gamma_base = 0;  // options.gamma, or 1/(3L)
     bool deterministic = false;
     bool plain_writes = false;
+    int sampling = 0;              // ASAGA_SAMPLE_UNIFORM or ASAGA_SAMPLE_PERMUTATION
     uint64_t seed = 0;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -201,6 +202,10 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
     if (o->epochs_per_segment < 0 || o->abar_recompute_every < 0 || o->max_warps < 0 ||
         o->column_stride < 0 || !(o->timeout_s >= 0))
         return fail(err, ASAGA_EINVAL, "negative option");
+    if (o->sampling != ASAGA_SAMPLE_UNIFORM && o->sampling != ASAGA_SAMPLE_PERMUTATION)
+        return fail(err, ASAGA_EINVAL, "unknown sampling");
+    if (o->sampling == ASAGA_SAMPLE_PERMUTATION && p->n > ((int64_t)1 << 62))
+        return fail(err, ASAGA_EINVAL, "permutation sampling needs n <= 2^62");
     if (!p->values || !p->labels) return fail(err, ASAGA_EINVAL, "values or labels is NULL");
     int64_t nnz = p->nnz;
     if (p->dense) {
@@ -388,6 +393,7 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     c->lambda = o->lambda;
     c->deterministic = o->deterministic != 0;
     c->plain_writes = o->plain_writes != 0;
+    c->sampling = o->sampling;
     c->seed = o->seed;
     c->epochs_per_segment = o->epochs_per_segment > 0 ? o->epochs_per_segment : 1;
     c->abar_every = o->abar_recompute_every;
@@ -547,6 +553,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.idx = nullptr;
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.plain_writes = c->plain_writes ? 1 : 0;
+    u.sampling = c->sampling;
     u.deadline_ns = 0;
     u.status = c->status;
     u.trace = nullptr;
@@ -691,60 +698,109 @@ asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, doub
     return ASAGA_OK;
 }
 
-// One trial of the autotuner: from x = 0, run epochs with (W, gamma) until
-// |grad f|^2 <= reduction * |grad f(0)|^2 (success), divergence, max_epochs,
-// or more update-kernel time than `give_up_ms`.  Returns the kernel time.
-asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, double reduction, int max_epochs,
-                        double give_up_ms, bool *success, double *t_ms, int *epochs, std::string *err,
-                        double *rate = nullptr) {
-    TRY(reset_state(c, err));
-    *success = false;
-    *t_ms = 0;
-    *epochs = 0;
-    if (rate) *rate = -1.0;
-    double g_min = g0, g_prev = g0;
-    bool monotone = true;
-    for (int e = 1; e <= max_epochs; ++e) {
-        double ms = 0, g = 0;
-        TRY(trial_epoch(c, W, gamma, &ms, &g, err));
-        *t_ms += ms;
-        *epochs = e;
-        if (!std::isfinite(g) || (e >= 3 && g > 4.0 * g_min)) return ASAGA_OK;  // diverging
-        g_min = std::min(g_min, g);
-        if (e >= max_epochs - 2 && g > g_prev) monotone = false;
-        g_prev = g;
-        // decrease of ln |grad f|^2 per second so far (used when no trial reaches the reduction)
-        if (rate && monotone && g < g0) *rate = std::log(g0 / g) / (*t_ms * 1e-3);
-        if (g <= reduction * g0) {
-            *success = true;
-            return ASAGA_OK;
-        }
-        if (*t_ms > give_up_ms) return ASAGA_OK;
+// ---------------------------------------------------------------------------
+// Autotuner.  Measured behaviour of asynchronous Sparse SAGA on a GB300 that
+// it relies on:
+//  * warps x step has a stability frontier: above it the iterate does not
+//    converge (logistic: |grad f|^2 bounces on a plateau; squared loss:
+//    divergence), below it the run converges, and near it the outcome
+//    varies from run to run;
+//  * below the frontier the epochs needed depend on the step, not on the
+//    number of warps;
+//  * the epoch time falls with the number of warps until the kernel saturates.
+// So the frontier is located at one warp count, and warp counts are then
+// raced along warps x step = constant, one notch inside the frontier.
+
+// log10 of |grad f|^2 / |grad f(x=0)|^2: the level the predictions aim at,
+// and the level that proves convergence in a frontier trial
+constexpr double kTuneDeep = -10.0;
+constexpr double kTuneConverged = -6.0;
+
+struct TuneTrial {
+    bool diverged = false;
+    int epochs = 0;
+    double t_ms = 0;                 // update-kernel time
+    std::vector<double> y;           // log10 |grad f|^2 / g0 after each epoch
+    double ms_per_epoch() const { return epochs > 0 ? t_ms / epochs : INFINITY; }
+};
+
+// Least-squares line through (e, y[e-1]) for e = first .. y.size().
+struct Trend {
+    double slope = 0, se = INFINITY, e_mean = 0, y_mean = 0;
+};
+Trend trend(const std::vector<double> &y, int first) {
+    Trend t;
+    const int m = (int)y.size(), k = m - first + 1;
+    if (k < 3) return t;
+    double se = 0, sy = 0;
+    for (int e = first; e <= m; ++e) {
+        se += e;
+        sy += y[e - 1];
     }
-    return ASAGA_OK;
+    t.e_mean = se / k;
+    t.y_mean = sy / k;
+    double sxx = 0, sxy = 0;
+    for (int e = first; e <= m; ++e) {
+        sxx += (e - t.e_mean) * (e - t.e_mean);
+        sxy += (e - t.e_mean) * (y[e - 1] - t.y_mean);
+    }
+    t.slope = sxy / sxx;
+    double rss = 0;
+    for (int e = first; e <= m; ++e) {
+        const double r = y[e - 1] - t.y_mean - t.slope * (e - t.e_mean);
+        rss += r * r;
+    }
+    t.se = std::sqrt(rss / std::max(1, k - 2) / sxx);
+    return t;
 }
 
-// Short stability trial: E epochs from x = 0; stable when |grad f|^2 fell
-// monotonically over the last two epochs and ended below half its start.
-asaga_status stability_trial(asaga_ctx *c, int W, double gamma, double g0, int E, bool *stable, double *t_ms,
-                             std::string *err) {
+// A frontier trial converges when |grad f|^2 reached kTuneConverged, or when
+// its trend from the fourth epoch on falls with t-statistic >= 3.5.  On the
+// plateau above the frontier |grad f|^2 bounces by one to two decades with
+// no trend, which this test rejects.
+bool converging(const TuneTrial &t) {
+    if (t.diverged) return false;
+    for (double v : t.y)
+        if (v <= kTuneConverged) return true;
+    const int m = (int)t.y.size();
+    const Trend tr = trend(t.y, std::max(3, m / 4));
+    return tr.slope < 0 && -tr.slope >= 3.5 * tr.se;
+}
+
+// Predicted epochs for |grad f|^2 to reach kTuneDeep: the first epoch that
+// reached it, else the least-squares trend of the trial's last two thirds,
+// if it falls with t-statistic >= 3 (INFINITY otherwise).
+double predict_epochs(const TuneTrial &t) {
+    if (t.diverged) return INFINITY;
+    const int m = (int)t.y.size();
+    for (int e = 1; e <= m; ++e)
+        if (t.y[e - 1] <= kTuneDeep) return e;
+    if (m < 5) return INFINITY;
+    const Trend tr = trend(t.y, std::max(3, m / 3));
+    if (!(tr.slope < -1e-3) || -tr.slope < 3.0 * tr.se) return INFINITY;
+    return std::max((double)m, tr.e_mean + (kTuneDeep - tr.y_mean) / tr.slope);
+}
+
+// One trial: from x = 0, up to E epochs at (W, gamma), |grad f|^2 after each.
+// Stops early on divergence, on reaching stop_level, or once the update time
+// exceeds give_up_ms.
+asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, int E, double stop_level, double give_up_ms,
+                        TuneTrial *out, std::string *err) {
     TRY(reset_state(c, err));
-    double g[3] = {g0, g0, g0};
-    *t_ms = 0;
-    *stable = false;
-    double g_min = g0;
+    TuneTrial t;
     for (int e = 1; e <= E; ++e) {
-        double ms = 0, g2 = 0;
-        const bool want = e >= E - 2 || e % 2 == 0;
-        TRY(trial_epoch(c, W, gamma, &ms, want ? &g2 : nullptr, err));
-        *t_ms += ms;
-        if (want) {
-            if (!std::isfinite(g2) || g2 > 4.0 * g_min) return ASAGA_OK;  // diverging
-            g_min = std::min(g_min, g2);
-            if (e >= E - 2) g[e - (E - 2)] = g2;
+        double ms = 0, g = 0;
+        TRY(trial_epoch(c, W, gamma, &ms, &g, err));
+        t.t_ms += ms;
+        t.epochs = e;
+        if (!std::isfinite(g) || g > 1e6 * g0) {
+            t.diverged = true;
+            break;
         }
+        t.y.push_back(std::log10(std::max(g / g0, 1e-300)));
+        if (t.y.back() <= stop_level || t.t_ms > give_up_ms) break;
     }
-    *stable = g[2] <= g[1] && g[1] <= g[0] && g[2] < 0.5 * g0;
+    *out = std::move(t);
     return ASAGA_OK;
 }
 
@@ -752,11 +808,11 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const int max_epochs = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 40;
-    const double reduction = 1e-6;  // candidates race to shrink |grad f|^2 by this factor
+    const int E_race = trial_epochs > 0 ? std::max(4, (int)std::ceil(trial_epochs)) : 24;
+    const int E_probe = std::min(16, E_race);
+    constexpr int kTop = -4, kBottom = 16;  // steps gamma0 * 2^(-k/2), k in [kTop, kBottom]
+    auto step = [&](int k) { return c->gamma_base * std::pow(2.0, -0.5 * k); };
     const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
-    std::vector<double> scales;  // step ladder gamma0 * 2^(-k/2), k = -4..16
-    for (int k = -4; k <= 16; ++k) scales.push_back(std::pow(2.0, -0.5 * k));
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -767,101 +823,85 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
     TRY(stream_sync(c, err));
     const double g0 = c->hout[2];
-
-    // 1. the stability frontier: largest stable step at a probe warp count
-    const int Wp = (int)std::min<int64_t>(cap, 256);
-    double frontier = 0;  // warps x scale
-    for (size_t k = 0; k < scales.size(); ++k) {
-        bool stable = false;
-        double t_ms = 0;
-        TRY(stability_trial(c, Wp, c->gamma_base * scales[k], g0, 6, &stable, &t_ms, err));
-        ++r.trials;
-        r.seconds += t_ms * 1e-3;
-        if (stable) {
-            frontier = Wp * scales[k];
-            break;
-        }
+    if (!(g0 > 0) || !std::isfinite(g0)) {  // x = 0 is already optimal: nothing to tune
+        if (res) *res = r;
+        return ASAGA_OK;
     }
-    if (frontier <= 0) {  // nothing stable even at the smallest step: keep the defaults
+    auto run = [&](int W, int k, int E, double stop_level, double give_up, TuneTrial *t) -> asaga_status {
+        TRY(tune_trial(c, W, step(k), g0, E, stop_level, give_up, t, err));
+        ++r.trials;
+        r.seconds += t->t_ms * 1e-3;
+        return ASAGA_OK;
+    };
+
+    // 1. the frontier at a probe warp count: bisection for the largest
+    //    converging step (k = kTop - 1 stands for "not converging", kBottom + 1
+    //    for "converging"); if no step converges, probe with 8x fewer warps
+    int Wp = (int)std::min<int64_t>(cap, 1024);
+    int kF = kBottom + 1;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        int lo = kTop - 1, hi = kBottom + 1;
+        while (hi - lo > 1) {
+            const int mid = lo + (hi - lo) / 2;
+            TuneTrial t;
+            TRY(run(Wp, mid, E_probe, kTuneConverged, INFINITY, &t));
+            if (converging(t)) hi = mid;
+            else lo = mid;
+        }
+        kF = hi;
+        if (kF <= kBottom || Wp == 1) break;
+        Wp = std::max(1, Wp / 8);
+    }
+    if (kF > kBottom) {  // no step converges visibly within the trials: keep the defaults
         TRY(reset_state(c, err));
         if (res) *res = r;
         return ASAGA_OK;
     }
-    // 2. race warp counts along the frontier (step = frontier / warps, snapped down
-    //    to the ladder), starting where the step reaches ~0.4 gamma0, outwards
-    auto snap = [&](double want) -> long {
-        for (size_t k = 0; k < scales.size(); ++k)
-            if (scales[k] <= want * (1 + 1e-12)) return (long)k;
-        return -1;
-    };
-    std::vector<int> pow2;
-    for (int64_t w = 4; w <= cap; w *= 2) pow2.push_back((int)w);
-    if (pow2.empty() || pow2.back() != cap) pow2.push_back((int)cap);
-    const double w_star = frontier / 0.4;
-    int centre = 0;
-    for (int j = 0; j < (int)pow2.size(); ++j)
-        if (std::fabs(std::log((double)pow2[j] / w_star)) < std::fabs(std::log((double)pow2[centre] / w_star))) centre = j;
+
+    // 2. race warp counts Wp * 2^j at k = kF + 2j + 1 (the same warps x step,
+    //    one notch inside the frontier; the step never above the ladder's top),
+    //    by predicted update time to reach kTuneDeep
     double best_ms = INFINITY;
-    long best_k = -1;
-    double best_rate = -1.0;  // fallback when no candidate reaches the reduction
-    long rate_k = -1;
-    int rate_w = 0;
-    auto try_w = [&](int W) -> asaga_status {
-        long k = snap(frontier / W);
-        if (k < 0) return ASAGA_OK;
-        for (int attempt = 0; attempt < 2 && k < (long)scales.size(); ++attempt, ++k) {
-            bool ok = false;
-            double t_ms = 0;
-            int ep = 0;
-            const double give_up = std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY;
-            double rate = -1.0;
-            TRY(tune_trial(c, W, c->gamma_base * scales[k], g0, reduction, max_epochs, give_up, &ok, &t_ms, &ep, err,
-                           &rate));
-            ++r.trials;
-            r.seconds += t_ms * 1e-3;
-            if (!ok && rate > best_rate) {
-                best_rate = rate;
-                rate_k = k;
-                rate_w = W;
-            }
-            if (ok) {
-                if (t_ms < best_ms) {
-                    best_ms = t_ms;
-                    best_k = k;
-                    r.warps = W;
-                }
-                return ASAGA_OK;
-            }
-            if (t_ms > give_up) return ASAGA_OK;  // slower than the best so far: do not back off further
+    int best_w = Wp, best_k = std::min(kBottom, kF + 2);  // used if no race trial settles
+    auto candidate = [&](int64_t W, int k, bool *improved) -> asaga_status {
+        *improved = false;
+        if (W < 1 || W > cap || k > kBottom) return ASAGA_OK;
+        TuneTrial t;
+        TRY(run((int)W, k, E_race, kTuneDeep, std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY, &t));
+        const double ms = predict_epochs(t) * t.ms_per_epoch();
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_w = (int)W;
+            best_k = k;
+            *improved = true;
         }
         return ASAGA_OK;
     };
-    TRY(try_w(pow2[centre]));
-    for (int j = centre + 1; j < (int)pow2.size(); ++j) {  // more warps, smaller steps
-        const double before = best_ms;
-        TRY(try_w(pow2[j]));
-        if (!(best_ms < before)) break;
+    auto warps_at = [&](int j) -> int64_t { return j >= 0 ? ((int64_t)Wp << j) : ((int64_t)Wp >> -j); };
+    auto k_at = [&](int j) { return std::max(kTop, kF + 2 * j + 1); };
+    bool improved = false;
+    TRY(candidate(warps_at(0), k_at(0), &improved));
+    for (int j = -1; warps_at(j) >= 1 && k_at(j + 1) > kTop; --j) {  // fewer warps, larger steps
+        TRY(candidate(warps_at(j), k_at(j), &improved));
+        if (!improved && std::isfinite(best_ms)) break;
     }
-    for (int j = centre - 1; j >= 0; --j) {  // fewer warps, larger steps
-        const double before = best_ms;
-        TRY(try_w(pow2[j]));
-        if (!(best_ms < before)) break;
+    for (int j = 1; warps_at(j) <= cap; ++j) {  // more warps, smaller steps
+        TRY(candidate(warps_at(j), k_at(j), &improved));
+        if (!improved && std::isfinite(best_ms)) break;
     }
-    if (best_k < 0 && rate_k >= 0) {  // slow problems: no candidate reached the reduction in time
-        best_k = rate_k;
-        r.warps = rate_w;
-        best_ms = std::log(1.0 / reduction) / best_rate * 1e3;
-    }
-    if (best_k >= 0) {
-        // one notch below the fastest step: asynchronous runs vary from run to run
-        r.gamma = c->gamma_base * scales[best_k] * std::sqrt(0.5);
-        r.score = std::log(1.0 / reduction) / (best_ms * 1e-3);
-    }
+    // 3. at the winning warp count, smaller steps while they are faster (well
+    //    conditioned problems need no more than a small step per update)
+    if (std::isfinite(best_ms))
+        for (int k = best_k + 1; k <= kBottom; ++k) {
+            TRY(candidate(best_w, k, &improved));
+            if (!improved) break;
+        }
+    if (std::isfinite(best_ms)) r.score = 1e3 / best_ms;
+    r.warps = best_w;
+    r.gamma = step(best_k);
     TRY(reset_state(c, err));
-    if (r.score > 0) {
-        c->warps = r.warps;
-        c->gamma = r.gamma;
-    }
+    c->warps = r.warps;
+    c->gamma = r.gamma;
     if (res) *res = r;
     return ASAGA_OK;
 }
@@ -1218,30 +1258,35 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
 // one notch lower as a margin.
 asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
     CK(cudaSetDevice(b->device), "cudaSetDevice");
-    const int E = trial_epochs > 0 ? std::max(3, (int)std::ceil(trial_epochs)) : 8;
+    const int E = trial_epochs > 0 ? std::max(5, (int)std::ceil(trial_epochs)) : 16;
+    constexpr int kTop = -4, kBottom = 12;
+    const int nk = kBottom - kTop + 1;
     TRY(batch_default_schedule(b, err));
-    std::vector<double> g0(b->count), best(b->count, -1.0), best_scale(b->count, 0.0);
-    auto grads = [&](std::vector<double> &g) -> asaga_status {
-        for (int i = 0; i < b->count; ++i) {
+    const int N = b->count;
+    std::vector<double> g0(N), g(N);
+    auto grads = [&](std::vector<double> &out) -> asaga_status {
+        for (int i = 0; i < N; ++i) {
             TRY(enqueue_grad(b->ctx[i], err));
             CK(cudaMemcpyAsync(b->ctx[i]->hout + 2, b->ctx[i]->dout + 2, sizeof(double), cudaMemcpyDeviceToHost,
                                b->stream), "copy");
         }
         TRY(stream_sync(b->ctx[0], err));
-        for (int i = 0; i < b->count; ++i) g[i] = b->ctx[i]->hout[2];
+        for (int i = 0; i < N; ++i) out[i] = b->ctx[i]->hout[2];
         return ASAGA_OK;
     };
     for (auto *c : b->ctx) TRY(reset_state(c, err));
     TRY(grads(g0));
+    // per instance and ladder position: converging?  predicted epochs to kTuneDeep
+    std::vector<char> conv((size_t)N * nk, 0), tried(nk, 0);
+    std::vector<double> pred((size_t)N * nk, INFINITY), best(N, INFINITY);
     int trials = 0;
     double seconds = 0;
-    for (int k = -4; k <= 8; ++k) {  // step ladder 4 gamma0 ... gamma0/16
+    for (int k = kTop; k <= kBottom; ++k) {  // steps gamma0_i * 2^(-k/2), shared k
         const double scale = std::pow(2.0, -0.5 * k);
         for (auto *c : b->ctx) TRY(reset_state(c, err));
-        std::vector<double> g1(b->count), g2(b->count), g3(b->count);
-        double t_ms = 0;
+        std::vector<TuneTrial> t(N);
         for (int e = 1; e <= E; ++e) {
-            for (int i = 0; i < b->count; ++i) {
+            for (int i = 0; i < N; ++i) {
                 asaga_ctx *c = b->ctx[i];
                 b->h_up[i].gamma = (float)(c->gamma_base * scale);
                 b->h_up[i].t_begin = (uint64_t)c->updates_done;
@@ -1249,36 +1294,61 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
             }
             float ms = 0;
             TRY(batch_segment(b, &ms, err));
-            t_ms += ms;
+            seconds += ms * 1e-3;
             for (auto *c : b->ctx) c->updates_done += c->n;
-            if (e == E - 2) TRY(grads(g1));
-            if (e == E - 1) TRY(grads(g2));
-            if (e == E) TRY(grads(g3));
-        }
-        ++trials;
-        seconds += t_ms * 1e-3;
-        bool any_better = false;
-        for (int i = 0; i < b->count; ++i) {
-            const bool stable = std::isfinite(g3[i]) && g3[i] <= g2[i] && g2[i] <= g1[i] && g3[i] < g0[i];
-            if (!stable) continue;
-            const double score = std::log(g0[i] / g3[i]);
-            if (score > best[i]) {
-                best[i] = score;
-                best_scale[i] = scale;
-                any_better = true;
+            TRY(grads(g));
+            for (int i = 0; i < N; ++i) {
+                if (t[i].diverged) continue;
+                t[i].epochs = e;
+                if (!(g0[i] > 0) || !std::isfinite(g[i]) || g[i] > 1e6 * g0[i]) {
+                    t[i].diverged = g0[i] > 0;
+                    continue;
+                }
+                t[i].y.push_back(std::log10(std::max(g[i] / g0[i], 1e-300)));
             }
         }
-        if (!any_better && k >= 2) break;  // smaller steps help no instance any more
+        ++trials;
+        tried[k - kTop] = 1;
+        bool any_better = false, all_settled = true;
+        for (int i = 0; i < N; ++i) {
+            conv[(size_t)i * nk + (k - kTop)] = converging(t[i]);
+            const double pe = predict_epochs(t[i]);
+            pred[(size_t)i * nk + (k - kTop)] = pe;
+            if (pe < best[i]) {
+                best[i] = pe;
+                any_better = true;
+            }
+            if (!std::isfinite(best[i])) all_settled = false;
+        }
+        if (!any_better && all_settled && k >= 2) break;  // smaller steps help no instance any more
     }
-    for (int i = 0; i < b->count; ++i) {
+    for (int i = 0; i < N; ++i) {
         asaga_ctx *c = b->ctx[i];
-        if (best[i] > 0) c->gamma = c->gamma_base * best_scale[i] * std::sqrt(0.5);
+        // the largest step that converges (and whose next smaller step does too),
+        // then the fastest predicted step at least one notch inside it
+        int kF = kBottom + 1;
+        for (int k = kTop; k <= kBottom && tried[k - kTop]; ++k) {
+            const bool next_ok = k == kBottom || !tried[k + 1 - kTop] || conv[(size_t)i * nk + (k + 1 - kTop)];
+            if (conv[(size_t)i * nk + (k - kTop)] && next_ok) {
+                kF = k;
+                break;
+            }
+        }
+        int kc = -1000;
+        double pc = INFINITY;
+        for (int k = kF + 1; k <= kBottom && tried[k - kTop]; ++k)
+            if (pred[(size_t)i * nk + (k - kTop)] < pc) {
+                pc = pred[(size_t)i * nk + (k - kTop)];
+                kc = k;
+            }
+        if (kc == -1000 && kF + 1 <= kBottom) kc = kF + 1;  // untried or unsettled: one notch inside
+        if (kc != -1000) c->gamma = c->gamma_base * std::pow(2.0, -0.5 * kc);
         c->warps = b->warps[i];
         TRY(reset_state(c, err));
         if (res) {
             res[i].warps = b->warps[i];
             res[i].gamma = c->gamma;
-            res[i].score = best[i] > 0 ? best[i] / (seconds / trials) : -1.0;
+            res[i].score = std::isfinite(pc) ? 1.0 / pc : -1.0;
             res[i].trials = trials;
             res[i].seconds = seconds;
         }
@@ -1310,6 +1380,7 @@ void asaga_default_options(asaga_options *o) {
     o->cuda_stream = nullptr;
     o->column_stride = 0;
     o->plain_writes = 0;
+    o->sampling = ASAGA_SAMPLE_UNIFORM;
 }
 
 asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {
@@ -1342,6 +1413,31 @@ asaga_status asaga_run(asaga_ctx *c, double max_epochs, double target, double f_
 asaga_status asaga_autotune(asaga_ctx *c, double trial_epochs, asaga_tune_result *res) {
     if (!c) return ASAGA_EINVAL;
     return autotune_impl(c, trial_epochs, res, &c->err);
+}
+
+asaga_status asaga_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
+                               int64_t *rows) {
+    std::string *err = &g_create_err;
+    if (n < 1) return fail(err, ASAGA_EINVAL, "n must be >= 1");
+    if (sampling != ASAGA_SAMPLE_UNIFORM && sampling != ASAGA_SAMPLE_PERMUTATION)
+        return fail(err, ASAGA_EINVAL, "unknown sampling");
+    if (sampling == ASAGA_SAMPLE_PERMUTATION && n > ((int64_t)1 << 62))
+        return fail(err, ASAGA_EINVAL, "permutation sampling needs n <= 2^62");
+    if (count < 0) return fail(err, ASAGA_EINVAL, "count < 0");
+    if (count == 0) return ASAGA_OK;
+    if (!rows) return fail(err, ASAGA_EINVAL, "rows is NULL");
+    int64_t *d_rows = nullptr;
+    cudaError_t e = cudaMalloc(&d_rows, (size_t)count * sizeof(int64_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(err, e == cudaErrorMemoryAllocation ? ASAGA_ENOMEM : ASAGA_ECUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    e = launch_sample_rows(seed, n, sampling, t_begin, count, d_rows, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(rows, d_rows, (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost);
+    cudaFree(d_rows);
+    if (e != cudaSuccess) return fail(err, ASAGA_ECUDA, std::string("sampler: ") + cudaGetErrorString(e));
+    return ASAGA_OK;
 }
 
 asaga_status asaga_measure_overlap(asaga_ctx *c, double epochs, asaga_overlap *out) {

@@ -34,6 +34,7 @@ struct UpdateParams {
     int loss;                 // 0 logistic, 1 squared
     float gamma, lambda, inv_n;
     uint64_t seed;            // sampler seed
+    int sampling;             // 0 uniform with replacement, 1 one permutation per epoch
     uint64_t t_begin;         // global index of this launch's first update
     int64_t count;            // updates in this launch
     int nwarps;               // warps taking part (static strided split)
@@ -72,6 +73,9 @@ constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in 
 void set_thread_error(const std::string &msg);
 
 // update.cu
+// rows[j] = the row of update t_begin + j (device buffer of count entries)
+cudaError_t launch_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
+                               int64_t *rows, cudaStream_t stream);
 cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
                           cudaStream_t s);
 int update_max_blocks_per_sm(int vtype, bool dense);

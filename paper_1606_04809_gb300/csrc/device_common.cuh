@@ -58,19 +58,58 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) used as a counter-based
-// generator: output number t of the stream with the given seed.
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
-    uint64_t z = seed + (t + 1) * 0x9E3779B97F4A7C15ull;
+// The output mix of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     return z ^ (z >> 31);
+}
+
+// SplitMix64 used as a counter-based generator: output number t+1 of the
+// stream seeded with `seed` (its state advances by the golden gamma).
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t t) {
+    return mix64(seed + (t + 1) * 0x9E3779B97F4A7C15ull);
 }
 
 // Row index of update t: uniform in [0, n) with replacement (Algorithm 2
 // samples i before reading anything), by multiply-high range reduction.
 __device__ __forceinline__ int64_t sample_row(uint64_t seed, uint64_t t, int64_t n) {
     return (int64_t)__umul64hi(splitmix64_at(seed, t), (uint64_t)n);
+}
+
+// Row index of update t when every epoch visits each row once: position
+// p = t mod n of epoch e = t / n goes through a 4-round balanced Feistel
+// network on 2h bits (4^h >= n) keyed by the epoch, and the network is
+// applied again until the value falls below n (cycle walking).  The network
+// is a bijection of [0, 4^h), so the walk from p < n reaches a value below n
+// within p's cycle; the iteration cap is never reached in practice (each
+// step lands below n with probability >= 1/4) and only keeps the loop bounded.
+__device__ __forceinline__ int64_t permuted_row(uint64_t seed, uint64_t t, int64_t n) {
+    constexpr uint64_t kGolden = 0x9E3779B97F4A7C15ull;
+    const uint64_t nn = (uint64_t)n;
+    const uint64_t e = t / nn, pos = t - e * nn;
+    const int bits = nn > 1 ? 64 - __clzll((long long)(nn - 1)) : 0;
+    const int h = bits > 1 ? (bits + 1) / 2 : 1;
+    const uint64_t mask = (1ull << h) - 1;
+    const uint64_t key = splitmix64_at(seed ^ 0xD1B54A32D192ED03ull, e);
+    uint64_t x = pos;
+    for (int walk = 0; walk < 4096; ++walk) {
+        uint64_t L = x >> h, R = x & mask;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const uint64_t f = mix64((key ^ R) + (uint64_t)(r + 1) * kGolden) & mask;
+            const uint64_t nl = R;
+            R = L ^ f;
+            L = nl;
+        }
+        x = (L << h) | R;
+        if (x < nn) return (int64_t)x;
+    }
+    return (int64_t)pos;
+}
+
+__device__ __forceinline__ int64_t sampled_row(int sampling, uint64_t seed, uint64_t t, int64_t n) {
+    return sampling == 1 ? permuted_row(seed, t, n) : sample_row(seed, t, n);
 }
 
 // phi'(z) in float32.  Logistic: -b / (1 + exp(b z)); squared: z - y.

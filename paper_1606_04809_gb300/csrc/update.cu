@@ -31,6 +31,8 @@
 // reduction updates x_v and abar_v.  Up to kRowCap entries of a row are
 // staged (lane l owns entries l, l+32, ...); longer rows read the rest
 // from global memory.
+#include <algorithm>
+
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -94,7 +96,7 @@ __device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool
         }
         return i;
     }
-    return sample_row(P.seed, P.t_begin + (uint64_t)t, P.n);
+    return sampled_row(P.sampling, P.seed, P.t_begin + (uint64_t)t, P.n);
 }
 
 // Lane 0 requests row i's row_ptr entries and label into meta slot m.
@@ -393,6 +395,20 @@ int update_max_blocks_per_sm(int vtype, bool dense) {
     case kF16: return dense ? occ<__half, true>() : occ<__half, false>();
     default: return 1;
     }
+}
+
+__global__ void sample_rows_kernel(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
+                                   int64_t *rows) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < count; j += (int64_t)gridDim.x * blockDim.x)
+        rows[j] = sampled_row(sampling, seed, t_begin + (uint64_t)j, n);
+}
+
+cudaError_t launch_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
+                               int64_t *rows, cudaStream_t stream) {
+    if (count <= 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>(4096, (count + 255) / 256);
+    sample_rows_kernel<<<grid, 256, 0, stream>>>(seed, n, sampling, t_begin, count, rows);
+    return cudaGetLastError();
 }
 
 }  // namespace asaga

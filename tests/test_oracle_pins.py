@@ -343,3 +343,83 @@ def test_serial_sparse_saga_is_stable_with_heavy_reweighting():
     xs = R.newton(p)
     res = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 9, ep), rel_tol=1e-12, max_epochs=3000)
     assert abs(res["fstar"] - R.objective(p, xs)) <= 1e-11 * abs(R.objective(p, xs))
+
+
+# ------------------------------------------------------------ lagged updates (App. C)
+
+@pytest.mark.parametrize("lam", [0.05, 0.0])
+def test_lagged_saga_equals_dense_saga(lam):
+    """The lagged scheme defers the steps x_v <- (1 - gamma lambda) x_v - gamma abar_v
+    of coordinates outside the sampled support; after the final catch-up it is
+    the dense SAGA iterate (Eq. SAGAupdate), step for step."""
+    p = tiny_sparse(n=30, d=12, k=3, seed=40, lam=lam)
+    st0 = consistent_state(p, seed=41)
+    idx = np.random.default_rng(42).integers(0, p.n, 90)
+    dense = st0.copy()
+    for i in idx:
+        R.dense_saga_step(p, dense, int(i), 0.15)
+    lag = R.lagged_saga(p, st0.copy(), idx, 0.15)
+    np.testing.assert_allclose(lag.x, dense.x, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(lag.abar, dense.abar, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(lag.alpha, dense.alpha, rtol=1e-12, atol=0)
+
+
+def test_lagged_pin_catches_a_missing_catch_up():
+    """A lagged step that forgot the deferred regulariser steps differs from
+    dense SAGA (the pin above can fail)."""
+    p = tiny_sparse(n=30, d=12, k=3, seed=40, lam=0.05)
+    st0 = consistent_state(p, seed=41)
+    idx = np.random.default_rng(42).integers(0, p.n, 90)
+    dense = st0.copy()
+    for i in idx:
+        R.dense_saga_step(p, dense, int(i), 0.15)
+    sparse_only = R.sparse_saga(p, st0.copy(), idx, 0.15, D=np.ones(p.d))
+    assert np.max(np.abs(sparse_only.x - dense.x)) > 1e-3
+
+
+def test_lagged_and_sparse_saga_converge_alike():
+    """App. C.1: on sparse data Sparse SAGA and lagged-update SAGA need about
+    the same number of passes over the data."""
+    p = synth.sparse_logistic(3000, 600, k_mean=8, k_min=2, k_max=30, zipf_s=1.1, values="abs_normal",
+                              storage="f64", seed=5, name="appC")
+    fs = R.objective(p, R.newton(p))
+    f0 = R.objective(p, np.zeros(p.d))
+    gamma = 1.0 / (3.0 * R.lipschitz(p))
+    sub = {}
+    for name, run in (("sparse", R.sparse_saga), ("lagged", R.lagged_saga)):
+        st = R.State.zeros(p)
+        curve = []
+        for ep in range(30):
+            run(p, st, synth.sample_indices(p.n, p.n, 7, ep), gamma)
+            curve.append((R.objective(p, st.x) - fs) / (f0 - fs))
+        sub[name] = np.array(curve)
+    assert sub["sparse"][-1] < 1e-7 and sub["lagged"][-1] < 1e-7
+    ratio = sub["sparse"][[9, 19, 29]] / sub["lagged"][[9, 19, 29]]
+    assert np.all((ratio > 0.1) & (ratio < 10)), ratio
+
+
+# ------------------------------------------------------------ row sampling
+
+def test_splitmix64_matches_its_published_outputs():
+    """The first outputs of the reference SplitMix64 for seed 1234567."""
+    assert R.splitmix64(1234567, 5) == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                                        4593380528125082431, 16408922859458223821]
+
+
+def test_sampler_takes_the_generator_outputs_in_order():
+    seed, n = 99, 1000
+    u = R.splitmix64(seed, 40)
+    rows = R.sampler_indices(seed, n, 0, 40)
+    assert rows.tolist() == [(v * n) >> 64 for v in u]
+    # a later window of the same stream
+    np.testing.assert_array_equal(R.sampler_indices(seed, n, 25, 15), rows[25:])
+
+
+def test_sampler_is_uniform_over_rows():
+    n, count = 50, 50000
+    rows = R.sampler_indices(7, n, 0, count)
+    assert rows.min() >= 0 and rows.max() < n
+    c = np.bincount(rows, minlength=n)
+    chi2 = np.sum((c - count / n) ** 2 / (count / n))
+    # chi-square with 49 degrees of freedom: P(chi2 > 90) < 1e-3
+    assert chi2 < 90, chi2
