@@ -15,7 +15,9 @@ gamma=1/(3L)), with the problem resident in HBM.  The line also reports:
                   -> asaga_destroy);
   roofline        algorithmic HBM bytes of the update kernel per launch over
                   its CUDA-event time, against the measured HBM peak;
-  cpu_baseline    the float64 CPU checker on a bounded sample, one host core.
+  cpu_baseline    the float64 CPU checker on a bounded sample, one host core;
+                  beside it (asaga_all_cores) lock-free ASAGA in C on every
+                  host core, the paper's own kind of implementation.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun (N > 1) every rank solves its own replica (weak scaling).
@@ -75,7 +77,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
-    ap.add_argument("--experiment", default=None, choices=["warps", "overlap", "cas"],
+    ap.add_argument("--experiment", default=None, choices=["warps", "overlap", "cas", "sampling"],
                     help="reproduce one of the paper's qualitative experiments instead of the benchmark")
     ap.add_argument("--warps", type=int, default=0, help="fixed concurrent warps (skips the autotuner)")
     ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
@@ -219,6 +221,34 @@ def time_checker(p, seconds, steps=None, warmup=0):
     return done / el, done, el
 
 
+def time_cpu_asaga(p, seconds, fstar, target):
+    """Multi-threaded lock-free ASAGA on all host cores (Algorithm 2 with the
+    compare-and-swap adds of App. G.2, C, float64): epochs/s of the updates and
+    the update time to `target` relative suboptimality (the float64 objective
+    after each epoch is not timed).  Runs until the target or `seconds`."""
+    from oracle import cpu_asaga
+    from oracle import reference as R
+    gamma = 1.0 / (3.0 * R.lipschitz(p))
+    run = cpu_asaga.Runner(p)
+    st = R.State.zeros(p)
+    upd, epochs, ttt = 0.0, 0, None
+    t_all = time.perf_counter()
+    while time.perf_counter() - t_all < seconds:
+        t0 = time.perf_counter()
+        run.run(st, p.n, gamma, seed=4)
+        upd += time.perf_counter() - t0
+        epochs += 1
+        if fstar is not None and (R.objective(p, st.x) - fstar) / abs(fstar) <= target:
+            ttt = upd
+            break
+    return {"value": epochs / upd, "unit": "epochs/s", "cores": run.threads,
+            "kind": "lock-free ASAGA on the host cores (Algorithm 2, CAS adds as in App. G.2), float64, C",
+            "gamma": gamma, "epochs": epochs, "update_seconds": upd,
+            "time_to_target": ({"target_rel_subopt": target, "seconds_updates": ttt, "epochs": epochs}
+                               if ttt is not None else None),
+            "sample": f"{epochs} epochs from x=0 ({upd:.1f} s of updates)"}
+
+
 def run_reference(args, p, wl):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -309,21 +339,25 @@ def run_batch(args):
         step = max(1, len(ps) // args.single_sample)
         sample = list(range(0, len(ps), step))[: args.single_sample]
         tot_dev = tot_wall = tot_tune = 0.0
-        statuses = []
+        statuses, failed = [], []
         for i in sample:
             with asaga.Context(ps[i], storage="f32", seed=i, abar_recompute_every=ABAR_EVERY,
                                cuda_stream=stream.cuda_stream) as c:
                 t0 = time.perf_counter()
-                asaga.asaga_autotune(c.ctx, 20)
+                tune1 = asaga.asaga_autotune(c.ctx, 20)
                 tot_tune += time.perf_counter() - t0
                 s1, r1 = asaga.asaga_run(c.ctx, 5000, TARGET, fs[i])
                 statuses.append(asaga.STATUS_NAMES[s1])
                 tot_dev += r1.solver_seconds + r1.eval_seconds
                 tot_wall += r1.seconds
+                if s1 != asaga.OK:
+                    failed.append({"instance": i, "n": ps[i].n, "d": ps[i].d, "lambda": ps[i].lam,
+                                   "status": asaga.STATUS_NAMES[s1], "epochs": r1.epochs,
+                                   "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"]})
         batch_sample = float(max(res[i].solver_seconds for i in sample))
         single = {"instances": len(sample), "storage": "f32", "sum_seconds_device": tot_dev,
                   "sum_seconds_wall": tot_wall, "autotune_wall_seconds": tot_tune,
-                  "all_ok": all(x == "ASAGA_OK" for x in statuses),
+                  "all_ok": all(x == "ASAGA_OK" for x in statuses), "failed": failed,
                   "batch_seconds_for_same_instances": batch_sample,
                   "batch_seconds_all_instances": batch_dev,
                   "speedup_batch_vs_single_same_instances": tot_dev / batch_sample if batch_sample > 0 else None}
@@ -347,7 +381,10 @@ def run_experiment(args):
                  warps, each at its fastest stable step (App. D.2, "theoretical speedups");
       overlap -- the overlap tau against the number of warps (App. E.2);
       cas     -- atomic against non-thread-safe updates: suboptimality reached and
-                 the abar bookkeeping error (App. G.2)."""
+                 the abar bookkeeping error (App. G.2);
+      sampling -- rows drawn with replacement (Algorithm 2) against one permutation
+                 per epoch, each autotuned, three seeds: epochs and device seconds
+                 to 1e-6."""
     import torch
     from paper_1606_04809_gb300 import asaga
     from paper_1606_04809_gb300 import build as lib_build
@@ -382,6 +419,16 @@ def run_experiment(args):
             with asaga.Context(p, storage=storage, seed=7, max_warps=W, gamma=0.01) as c:
                 o = asaga.asaga_measure_overlap(c.ctx, 0.05 if W == 1 else 1.0)
             rows.append(o)
+    elif args.experiment == "sampling":
+        for sampling in ("uniform", "permutation"):
+            for seed in (1, 2, 3):
+                with asaga.Context(p, storage=storage, seed=seed, sampling=sampling,
+                                   abar_recompute_every=ABAR_EVERY) as c:
+                    tune = asaga.asaga_autotune(c.ctx)
+                    s, r = asaga.asaga_run(c.ctx, 300, TARGET, fstar)
+                rows.append({"sampling": sampling, "seed": seed, "status": asaga.STATUS_NAMES[s],
+                             "warps": tune["warps"], "gamma": tune["gamma"], "epochs": r.epochs,
+                             "seconds_device": r.solver_seconds + r.eval_seconds})
     else:  # cas
         for plain in (0, 1):
             with asaga.Context(p, storage=storage, seed=7, max_warps=1024, gamma=0.05, plain_writes=plain,
@@ -530,6 +577,8 @@ def main():
         eps, done, el = time_checker(p, args.cpu_seconds)
         cpu = {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0 ({el:.1f} s)"}
+        cpu["asaga_all_cores"] = time_cpu_asaga(p, args.cpu_seconds * 2,
+                                                golden["fstar"] if golden else None, TARGET)
 
     a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
     if rank == 0:

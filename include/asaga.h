@@ -160,6 +160,8 @@ typedef struct {
     int64_t max_row_len; /* longest row                                          */
     int n_hot;           /* frequent columns accumulated in shared memory by the
                             float64 scatters                                    */
+    int warps_per_block; /* update kernel blocks: 8 warps, or fewer when the
+                            autotuner found the warps faster spread over the SMs */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */
@@ -206,7 +208,9 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  * falls with the number of warps.  Steps are gamma0 * 2^(-k/2), gamma0 =
  * options.gamma or 1/(3L), k = -4..16.  Each trial starts from x = 0,
  * alpha = 0 and records the float64 |grad f|^2 after every epoch:
- *  1. frontier: at min(1024, n/4, resident) warps, bisection over k for the
+ *  1. frontier: at min(1024, n/32, resident) warps (Theorem 2 asks for
+ *     tau < n/10, and tau measures 1.5 to 4 times the warps; no candidate
+ *     exceeds n/32 warps), bisection over k for the
  *     largest step whose 16-epoch trial converges (|grad f|^2 shrinks by
  *     1e6, or its log falls with a least-squares t-statistic >= 3.5);
  *     if none does, again with 8x fewer warps (twice at most);
@@ -214,8 +218,14 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  *     (W x step constant), scored by the predicted update time for
  *     |grad f|^2 to shrink by 1e10 (the least-squares trend of the trial's
  *     last two thirds, if its t-statistic is >= 3); trials run trial_epochs
- *     epochs (<= 0: 24) and stop when slower than 1.5x the best so far;
- *  3. smaller steps at the winning warp count while they score better.
+ *     epochs (<= 0: 24), more (up to 8x, within 250 ms of update time)
+ *     while the prediction lies beyond twice their length, and stop when
+ *     slower than 1.5x the best so far;
+ *     A candidate with fewer warps (a larger step) wins within a 1.2x
+ *     tolerance, one with more warps must be 1.2x faster;
+ *  3. smaller steps at the winning warp count while they score better;
+ *  4. the update kernel's block shape at the winner: eight warps per block
+ *     or the warps spread evenly over the SMs, whichever epoch is faster.
  * If no trial converges, the defaults stay.  score = 1 / (predicted
  * seconds of the winner), -1 when none settled.  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
@@ -325,7 +335,8 @@ typedef struct asaga_batch asaga_batch;
  * the sparse or dense layout, options[0].epochs_per_segment and
  * options[0].abar_recompute_every, and run on options[0].cuda_stream.  The
  * initial schedule gives instance i warps in proportion to its nonzeros (a
- * multiple of 4, at least 4, at most max(4, n_i/16)) within the warps that
+ * multiple of 4, at least 4, at most max(4, n_i/32), which keeps tau near
+ * n_i/10 as Theorem 2 asks) within the warps that
  * can be resident at once.  EINVAL as asaga_create, or for mixed dtypes or
  * layouts, deterministic options, or count < 1. */
 asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_problem *problems,

@@ -1,4 +1,5 @@
-"""Builds the C part of the CPU checker (test infrastructure only).
+"""Builds the C part of the CPU checker and the multi-threaded CPU ASAGA
+baseline into one library (test infrastructure only).
 
 gcc, -O2, no fast-math and no floating-point contraction, so that the float64
 results are the same on x86-64 and aarch64 hosts.
@@ -9,18 +10,18 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "saga_ref.c")
+SRCS = [os.path.join(HERE, "saga_ref.c"), os.path.join(HERE, "asaga_cpu.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libasaga_oracle.so")
 
 
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in SRCS):
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
-           SRC, "-o", tmp, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-pthread",
+           *SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

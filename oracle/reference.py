@@ -263,6 +263,43 @@ def sampler_indices(seed: int, n: int, t_begin: int, count: int) -> np.ndarray:
     return rows
 
 
+def _mix64(z: int) -> int:
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def permutation_indices(seed: int, n: int, t_begin: int, count: int) -> np.ndarray:
+    """Rows of updates t_begin .. t_begin+count-1 when every epoch visits each
+    row once (a sampling variant the paper does not use; the solver's
+    specification of it is restated here): epoch e = t // n sends position
+    p = t - e n through a 4-round balanced Feistel network on 2h bits
+    (4^h >= n, h >= 1), keyed by the (e+1)-th SplitMix64 output for seed xor
+    0xD1B54A32D192ED03, repeating the network until the value is below n."""
+    b = (n - 1).bit_length()
+    h = max(1, (b + 1) // 2)
+    mask = (1 << h) - 1
+    rows = np.empty(count, dtype=np.int64)
+    keys = {}
+    for j in range(count):
+        t = t_begin + j
+        e, pos = divmod(t, n)
+        if e not in keys:
+            keys[e] = _mix64(((seed ^ 0xD1B54A32D192ED03) + (e + 1) * _SPLITMIX_GAMMA) & _M64)
+        key = keys[e]
+        x = pos
+        while True:
+            left, right = x >> h, x & mask
+            for r in range(4):
+                f = _mix64(((key ^ right) + (r + 1) * _SPLITMIX_GAMMA) & _M64) & mask
+                left, right = right, left ^ f
+            x = (left << h) | right
+            if x < n:
+                break
+        rows[j] = x
+    return rows
+
+
 def row_derivatives(p, x: np.ndarray) -> np.ndarray:
     """phi'_i(a_i.x) for every i, row by row in float64 (C)."""
     out = np.empty(p.n)

@@ -66,7 +66,7 @@ class asaga_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64), ("L", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("warps", ctypes.c_int),
                 ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
-                ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int)]
+                ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("warps_per_block", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -36,6 +36,7 @@ struct asaga_ctx {
     bool deterministic = false;
     bool plain_writes = false;
     int sampling = 0;              // ASAGA_SAMPLE_UNIFORM or ASAGA_SAMPLE_PERMUTATION
+    bool spread = false;           // update kernel: warps spread over the SMs (else 8 per block)
     uint64_t seed = 0;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -560,9 +561,20 @@ UpdateParams update_params(const asaga_ctx *c) {
     return u;
 }
 
+int update_warps_per_block(const asaga_ctx *c, int nwarps) {
+    if (nwarps <= 1) return 1;
+    const int per_sm = (nwarps + c->sms - 1) / std::max(1, c->sms);
+    return c->spread ? std::min(kUpdateBlock / 32, std::max(1, per_sm)) : kUpdateBlock / 32;
+}
+
 asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
-    const int block = u.nwarps == 1 ? 32 : kUpdateBlock;
-    const int wpb = block / 32;
+    // eight warps to a block, or (c->spread) the warps spread evenly over
+    // the SMs, one block per SM while they allow: then each SM's load/store
+    // units and outstanding misses serve fewer warps, which helps a
+    // latency-bound state larger than L2 and not a small hot-line-bound one
+    // (the autotuner times both)
+    const int wpb = update_warps_per_block(c, u.nwarps);
+    const int block = 32 * wpb;
     const int grid = (u.nwarps + wpb - 1) / wpb;
     CK(launch_update(u, c->vtype, c->dense, grid, block, c->stream), "update kernel");
     ++c->launches;
@@ -715,6 +727,10 @@ asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, doub
 // and the level that proves convergence in a frontier trial
 constexpr double kTuneDeep = -10.0;
 constexpr double kTuneConverged = -6.0;
+// update time a race trial may spend beyond its first trial_epochs epochs
+constexpr double kTuneExtendMs = 250.0;
+// predicted-time tolerance in favour of fewer warps (and larger steps)
+constexpr double kTuneFewerWarps = 1.2;
 
 struct TuneTrial {
     bool diverged = false;
@@ -781,27 +797,32 @@ double predict_epochs(const TuneTrial &t) {
     return std::max((double)m, tr.e_mean + (kTuneDeep - tr.y_mean) / tr.slope);
 }
 
-// One trial: from x = 0, up to E epochs at (W, gamma), |grad f|^2 after each.
-// Stops early on divergence, on reaching stop_level, or once the update time
-// exceeds give_up_ms.
+// Trial epochs at (W, gamma), appended to t: |grad f|^2 after each.  Stops
+// early on divergence, on reaching stop_level, or once the trial's update
+// time exceeds give_up_ms.
+asaga_status trial_epochs_run(asaga_ctx *c, int W, double gamma, double g0, int E, double stop_level,
+                              double give_up_ms, TuneTrial *t, std::string *err) {
+    for (int e = 0; e < E && !t->diverged; ++e) {
+        double ms = 0, g = 0;
+        TRY(trial_epoch(c, W, gamma, &ms, &g, err));
+        t->t_ms += ms;
+        t->epochs += 1;
+        if (!std::isfinite(g) || g > 1e6 * g0) {
+            t->diverged = true;
+            break;
+        }
+        t->y.push_back(std::log10(std::max(g / g0, 1e-300)));
+        if (t->y.back() <= stop_level || t->t_ms > give_up_ms) break;
+    }
+    return ASAGA_OK;
+}
+
+// One trial: from x = 0, up to E epochs (see trial_epochs_run).
 asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, int E, double stop_level, double give_up_ms,
                         TuneTrial *out, std::string *err) {
     TRY(reset_state(c, err));
-    TuneTrial t;
-    for (int e = 1; e <= E; ++e) {
-        double ms = 0, g = 0;
-        TRY(trial_epoch(c, W, gamma, &ms, &g, err));
-        t.t_ms += ms;
-        t.epochs = e;
-        if (!std::isfinite(g) || g > 1e6 * g0) {
-            t.diverged = true;
-            break;
-        }
-        t.y.push_back(std::log10(std::max(g / g0, 1e-300)));
-        if (t.y.back() <= stop_level || t.t_ms > give_up_ms) break;
-    }
-    *out = std::move(t);
-    return ASAGA_OK;
+    *out = TuneTrial();
+    return trial_epochs_run(c, W, gamma, g0, E, stop_level, give_up_ms, out, err);
 }
 
 asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
@@ -812,7 +833,9 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     const int E_probe = std::min(16, E_race);
     constexpr int kTop = -4, kBottom = 16;  // steps gamma0 * 2^(-k/2), k in [kTop, kBottom]
     auto step = [&](int k) { return c->gamma_base * std::pow(2.0, -0.5 * k); };
-    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 4));
+    // Theorem 2 wants the overlap tau below n/10; measured, tau is 1.5 to 4
+    // times the number of warps: at most n/32 warps
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 32));
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -867,9 +890,27 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         *improved = false;
         if (W < 1 || W > cap || k > kBottom) return ASAGA_OK;
         TuneTrial t;
-        TRY(run((int)W, k, E_race, kTuneDeep, std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY, &t));
+        const double give_up = std::isfinite(best_ms) ? 1.5 * best_ms : INFINITY;
+        TRY(run((int)W, k, E_race, kTuneDeep, give_up, &t));
+        // a prediction far beyond the trial extrapolates the early, fast phase
+        // of an ill-conditioned problem: run on (up to 8x the epochs, while
+        // the trial is cheap) until the prediction is within 2x of its length
+        while (!t.diverged && t.epochs < 8 * E_race && t.t_ms < std::min(give_up, kTuneExtendMs)) {
+            const double pe = predict_epochs(t);
+            if (!std::isfinite(pe) || pe <= 2.0 * t.epochs || t.y.back() <= kTuneDeep) break;
+            const double before = t.t_ms;
+            TRY(trial_epochs_run(c, (int)W, step(k), g0, std::max(1, t.epochs / 4), kTuneDeep, give_up, &t, err));
+            r.seconds += (t.t_ms - before) * 1e-3;
+        }
         const double ms = predict_epochs(t) * t.ms_per_epoch();
-        if (ms < best_ms) {
+        // fewer warps and a larger step win within a tolerance: the step
+        // carries the slow tail of an ill-conditioned problem beyond the
+        // trial, and the overlap tau is smaller
+        const bool better = !std::isfinite(best_ms) ? std::isfinite(ms)
+                            : W < best_w        ? ms < kTuneFewerWarps * best_ms
+                            : W > best_w        ? ms * kTuneFewerWarps < best_ms
+                                                : ms < best_ms;
+        if (better) {
             best_ms = ms;
             best_w = (int)W;
             best_k = k;
@@ -896,6 +937,23 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
             TRY(candidate(best_w, k, &improved));
             if (!improved) break;
         }
+    // 4. the block shape at the winner: eight warps per block or the warps
+    //    spread over the SMs (the faster of two timed epochs each)
+    c->spread = false;
+    if (std::isfinite(best_ms) && (best_w + c->sms - 1) / std::max(1, c->sms) < kUpdateBlock / 32) {
+        double t_shape[2] = {INFINITY, INFINITY};
+        for (int shape = 0; shape < 2; ++shape) {
+            c->spread = shape == 1;
+            TRY(reset_state(c, err));
+            for (int e = 0; e < 3; ++e) {
+                double ms = 0;
+                TRY(trial_epoch(c, best_w, step(best_k), &ms, nullptr, err));
+                r.seconds += ms * 1e-3;
+                if (e > 0) t_shape[shape] = std::min(t_shape[shape], ms);
+            }
+        }
+        c->spread = t_shape[1] < 0.98 * t_shape[0];
+    }
     if (std::isfinite(best_ms)) r.score = 1e3 / best_ms;
     r.warps = best_w;
     r.gamma = step(best_k);
@@ -1067,7 +1125,7 @@ asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
         const asaga_ctx *c = b->ctx[i];
         const double share = (double)std::max<int64_t>(c->nnz, c->n) / total * (double)budget;
         int64_t w = std::max<int64_t>(4, ((int64_t)share / 4) * 4);
-        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 16 / 4) * 4));
+        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 32 / 4) * 4));  // tau below ~n/10 (Theorem 2)
         b->warps[i] = (int)w;
         used += w;
     }
@@ -1528,6 +1586,7 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->device_bytes = c->device_bytes;
     info->max_row_len = c->max_row_len;
     info->n_hot = c->n_hot;
+    info->warps_per_block = update_warps_per_block(c, c->warps);
     return ASAGA_OK;
 }
 
@@ -1608,7 +1667,10 @@ asaga_status asaga_batch_get_info(asaga_batch *b, int i, asaga_info *info) {
     if (!b) return ASAGA_EINVAL;
     if (i < 0 || i >= b->count) return fail(&b->err, ASAGA_EINVAL, "instance out of range");
     asaga_status s = asaga_get_info(b->ctx[i], info);
-    if (s == ASAGA_OK) info->warps = b->warps[i];
+    if (s == ASAGA_OK) {
+        info->warps = b->warps[i];
+        info->warps_per_block = kBatchBlock / 32;
+    }
     return s;
 }
 

@@ -76,6 +76,7 @@ def test_invalid_csr_is_rejected(lib, mutate, msg):
     (dict(storage_dtype="f64"), "storage_dtype"),
     (dict(loss=7), "loss"),
     (dict(max_warps=-2), "negative"),
+    (dict(sampling=5), "sampling"),
 ])
 def test_invalid_options_are_rejected(lib, opt, msg):
     s, err = create(*small_csr(), **opt)
@@ -133,3 +134,17 @@ def test_validation_of_a_large_problem_reports_the_first_bad_row(lib):
     bad2[299_999, 3] = d
     s, err = create(row_ptr, bad2.ravel(), vals, y, n=n, d=d)
     assert s == asaga.EINVAL and str(299_999 * k + 3) in err
+
+
+def test_sampler_arguments_are_checked_before_any_cuda_call(lib):
+    L = asaga.load()
+    rows = np.empty(4, dtype=np.int64)
+    p = rows.ctypes.data
+    assert L.asaga_sample_rows(1, 0, 0, 0, 4, p) == asaga.EINVAL
+    assert "n must be" in asaga.asaga_last_error(None)
+    assert L.asaga_sample_rows(1, 10, 2, 0, 4, p) == asaga.EINVAL
+    assert "sampling" in asaga.asaga_last_error(None)
+    assert L.asaga_sample_rows(1, 10, 0, 0, -1, p) == asaga.EINVAL
+    assert L.asaga_sample_rows(1, 10, 0, 0, 4, None) == asaga.EINVAL
+    assert L.asaga_sample_rows(1, (1 << 62) + 1, 1, 0, 4, p) == asaga.EINVAL
+    assert L.asaga_sample_rows(1, 10, 0, 0, 0, None) == asaga.OK  # nothing to do

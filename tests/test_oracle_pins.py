@@ -423,3 +423,51 @@ def test_sampler_is_uniform_over_rows():
     chi2 = np.sum((c - count / n) ** 2 / (count / n))
     # chi-square with 49 degrees of freedom: P(chi2 > 90) < 1e-3
     assert chi2 < 90, chi2
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 16, 17, 1000, 4097])
+def test_permutation_sampling_visits_every_row_once_per_epoch(n):
+    rows = R.permutation_indices(12, n, 0, 3 * n)
+    for e in range(3):
+        assert sorted(rows[e * n:(e + 1) * n].tolist()) == list(range(n))
+    if n >= 16:  # the epochs differ from each other and from the identity
+        assert not np.array_equal(rows[:n], rows[n:2 * n])
+        assert not np.array_equal(rows[:n], np.arange(n))
+    # a window that starts mid-epoch is the same stream
+    np.testing.assert_array_equal(R.permutation_indices(12, n, n // 2 + 1, n), rows[n // 2 + 1:n // 2 + 1 + n])
+
+
+def test_permutation_positions_are_spread_over_rows():
+    """Over many epochs, the row at a fixed position is close to uniform."""
+    n, epochs = 20, 4000
+    first = np.array([R.permutation_indices(5, n, e * n, 1)[0] for e in range(epochs)])
+    c = np.bincount(first, minlength=n)
+    chi2 = np.sum((c - epochs / n) ** 2 / (epochs / n))
+    assert chi2 < 50, chi2  # 19 degrees of freedom: P(chi2 > 50) < 1e-3
+
+
+# ------------------------------------------------------------ multi-threaded CPU ASAGA (timing baseline)
+
+def test_cpu_asaga_on_one_thread_is_serial_sparse_saga():
+    from oracle import cpu_asaga
+    p = synth.small_logistic()
+    gamma = 1.0 / (3.0 * R.lipschitz(p))
+    run = cpu_asaga.Runner(p, threads=1)
+    st = run.run(R.State.zeros(p), 2 * p.n, gamma, seed=17)
+    ref = R.sparse_saga(p, R.State.zeros(p), R.sampler_indices(17, p.n, 0, 2 * p.n), gamma)
+    # alpha_i += delta instead of alpha_i = phi'_i: equal up to one rounding per visit
+    np.testing.assert_allclose(st.x, ref.x, rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(st.abar, ref.abar, rtol=1e-10, atol=1e-14)
+
+
+def test_cpu_asaga_with_threads_reaches_the_optimum():
+    from oracle import cpu_asaga
+    p = synth.small_logistic()
+    fs = R.objective(p, R.newton(p))
+    gamma = 1.0 / (3.0 * R.lipschitz(p))
+    run = cpu_asaga.Runner(p, threads=4)
+    st = R.State.zeros(p)
+    for _ in range(60):
+        run.run(st, p.n, gamma, seed=3)
+    assert (R.objective(p, st.x) - fs) / abs(fs) < 1e-8
+    assert np.max(np.abs(st.abar - R.abar_from_scratch(p, st.alpha))) < 1e-10
