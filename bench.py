@@ -353,7 +353,8 @@ def run_batch(args):
                 if s1 != asaga.OK:
                     failed.append({"instance": i, "n": ps[i].n, "d": ps[i].d, "lambda": ps[i].lam,
                                    "status": asaga.STATUS_NAMES[s1], "epochs": r1.epochs,
-                                   "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"]})
+                                   "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"],
+                                   "tune_score": tune1["score"], "tune_trials": tune1["trials"]})
         batch_sample = float(max(res[i].solver_seconds for i in sample))
         single = {"instances": len(sample), "storage": "f32", "sum_seconds_device": tot_dev,
                   "sum_seconds_wall": tot_wall, "autotune_wall_seconds": tot_tune,

@@ -222,8 +222,12 @@ asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subo
  *     while the prediction lies beyond twice their length, and stop when
  *     slower than 1.5x the best so far;
  *     A candidate with fewer warps (a larger step) wins within a 1.2x
- *     tolerance, one with more warps must be 1.2x faster;
- *  3. smaller steps at the winning warp count while they score better;
+ *     tolerance, one with more warps must be 1.2x faster.  If no candidate
+ *     settles, the race is run again one notch further inside (twice at
+ *     most);
+ *  3. smaller steps at the winning warp count while they score better, then
+ *     a confirmation trial of twice the length that must still show a
+ *     downward trend (else one notch smaller a step, three times at most);
  *  4. the update kernel's block shape at the winner: eight warps per block
  *     or the warps spread evenly over the SMs, whichever epoch is faster.
  * If no trial converges, the defaults stay.  score = 1 / (predicted

@@ -921,14 +921,21 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     auto warps_at = [&](int j) -> int64_t { return j >= 0 ? ((int64_t)Wp << j) : ((int64_t)Wp >> -j); };
     auto k_at = [&](int j) { return std::max(kTop, kF + 2 * j + 1); };
     bool improved = false;
-    TRY(candidate(warps_at(0), k_at(0), &improved));
-    for (int j = -1; warps_at(j) >= 1 && k_at(j + 1) > kTop; --j) {  // fewer warps, larger steps
-        TRY(candidate(warps_at(j), k_at(j), &improved));
-        if (!improved && std::isfinite(best_ms)) break;
-    }
-    for (int j = 1; warps_at(j) <= cap; ++j) {  // more warps, smaller steps
-        TRY(candidate(warps_at(j), k_at(j), &improved));
-        if (!improved && std::isfinite(best_ms)) break;
+    // a frontier read too optimistically leaves every candidate on the
+    // plateau: race again one notch further inside (twice at most)
+    for (int retry = 0; retry < 3 && !std::isfinite(best_ms); ++retry, ++kF) {
+        if (kF + 1 > kBottom) break;
+        best_w = Wp;
+        best_k = std::min(kBottom, kF + 2);
+        TRY(candidate(warps_at(0), k_at(0), &improved));
+        for (int j = -1; warps_at(j) >= 1 && k_at(j + 1) > kTop; --j) {  // fewer warps, larger steps
+            TRY(candidate(warps_at(j), k_at(j), &improved));
+            if (!improved && std::isfinite(best_ms)) break;
+        }
+        for (int j = 1; warps_at(j) <= cap; ++j) {  // more warps, smaller steps
+            TRY(candidate(warps_at(j), k_at(j), &improved));
+            if (!improved && std::isfinite(best_ms)) break;
+        }
     }
     // 3. at the winning warp count, smaller steps while they are faster (well
     //    conditioned problems need no more than a small step per update)
@@ -936,6 +943,17 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         for (int k = best_k + 1; k <= kBottom; ++k) {
             TRY(candidate(best_w, k, &improved));
             if (!improved) break;
+        }
+    // confirmation: the winner over a trial twice as long must still show a
+    // downward trend (a plateau can set in after a short trial's early
+    // progress); one notch smaller a step while it does not (three times at most)
+    if (std::isfinite(best_ms))
+        for (int attempt = 0; attempt < 3 && best_k <= kBottom; ++attempt) {
+            TuneTrial t;
+            TRY(run(best_w, best_k, 2 * E_race, kTuneDeep, std::max(4.0 * kTuneExtendMs, 3.0 * best_ms), &t));
+            if (!t.diverged && std::isfinite(predict_epochs(t))) break;
+            if (best_k == kBottom) break;
+            ++best_k;
         }
     // 4. the block shape at the winner: eight warps per block or the warps
     //    spread over the SMs (the faster of two timed epochs each)
