@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--experiment", default=None, choices=["warps", "overlap", "cas", "sampling"],
                     help="reproduce one of the paper's qualitative experiments instead of the benchmark")
     ap.add_argument("--warps", type=int, default=0, help="fixed concurrent warps (skips the autotuner)")
+    ap.add_argument("--compact", type=int, default=0, choices=[0, 1],
+                    help="compact storage of A (uint16 indices / one value per row where exact)")
     ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
     return ap.parse_args()
 
@@ -184,14 +186,17 @@ def ncu_traffic(workload):
         return None
 
 
-def update_hbm_bytes(p, storage):
+def update_hbm_bytes(p, storage, info=None):
     """Algorithmic HBM bytes of one epoch of updates: each sampled row reads
-    its CSR slice (4 B index + value) once, row_ptr (2 x 8 B), its label
-    (4 B) and swaps alpha_i (4 B read + 4 B write).  The per-column state is
+    its CSR slice (index + value per entry; 2-byte indices and one value per
+    row in the compact layout) once, row_ptr (2 x 8 B), its label (4 B) and
+    swaps alpha_i (4 B read + 4 B write).  The per-column state is
     L2-resident by design and not counted."""
     vsz = {"f32": 4, "bf16": 2, "f16": 2}[storage]
-    per_nnz = vsz + (0 if p.dense else 4)
-    per_row = (0 if p.dense else 16) + 4 + 8
+    idx = 0 if p.dense else (info["col_index_bytes"] if info else 4)
+    row_values = bool(info and info["row_values"])
+    per_nnz = (0 if row_values else vsz) + idx
+    per_row = (0 if p.dense else 16) + 4 + 8 + (4 if row_values else 0)
     return p.nnz * per_nnz + p.n * per_row
 
 
@@ -479,7 +484,8 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    opts = dict(seed=1000 + rank, abar_recompute_every=ABAR_EVERY, cuda_stream=stream.cuda_stream)
+    opts = dict(seed=1000 + rank, abar_recompute_every=ABAR_EVERY, cuda_stream=stream.cuda_stream,
+                compact=args.compact)
     ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
     # schedule: concurrent warps and step size picked by the native autotuner
     if args.warps > 0:
@@ -519,11 +525,10 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    ctx.close()
 
     value = world * args.steps / (ms * 1e-3)
     upd_ms = 1e3 * solver_s / args.steps
-    hbm_bytes = update_hbm_bytes(p, storage)
+    hbm_bytes = update_hbm_bytes(p, storage, info)
     peak, peak_kind = measured_peak_hbm()
     achieved = hbm_bytes / (upd_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -537,12 +542,15 @@ def main():
         if golden is None:
             ttt = {"status": "skipped", "reason": why}
         else:
-            with asaga.Context(p, storage=storage, **opts) as c2:
-                s, r = asaga.asaga_run(c2.ctx, 200, TARGET, golden["fstar"])
+            # the timed context itself, reset to x = 0 (it keeps the tuned schedule and block shape)
+            asaga.asaga_set_state(ctx.ctx, np.zeros(p.d, np.float32), np.zeros(p.d, np.float32),
+                                  np.zeros(p.n, np.float32), 0)
+            s, r = asaga.asaga_run(ctx.ctx, 200, TARGET, golden["fstar"])
             ttt = {"target_rel_subopt": TARGET, "status": asaga.STATUS_NAMES[s], "epochs": r.epochs,
                    "seconds_wall": r.seconds, "seconds_device": r.solver_seconds + r.eval_seconds,
                    "solver_seconds": r.solver_seconds, "eval_seconds": r.eval_seconds,
                    "rel_subopt": r.rel_subopt, "fstar": golden["fstar"], "fstar_bound": golden["bound"]}
+    ctx.close()
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -588,7 +596,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
-                       "warps": info["warps"], "gamma": info["gamma"], "abar_recompute_every": ABAR_EVERY,
+                       "warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
+                       "abar_recompute_every": ABAR_EVERY, "compact": args.compact,
+                       "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"],
                        "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "time_to_target": ttt,

@@ -113,6 +113,13 @@ typedef struct {
  *                        ASAGA_SAMPLE_PERMUTATION: every epoch visits each row
  *                        once, in a seeded pseudo-random order (a variant
  *                        the paper does not analyse; see asaga_sample_rows).
+ *   compact              1 = store A compactly where that changes no number
+ *                        the solver computes with: uint16 column indices when
+ *                        d <= 65536, and one float32 value per row when every
+ *                        stored value of each row is equal (binary rows
+ *                        scaled to unit norm); 0 (default) = int32 indices and
+ *                        one value per entry.  A batch compacts only what all
+ *                        its instances allow (options[0].compact).
  */
 typedef struct {
     asaga_loss loss;
@@ -129,6 +136,7 @@ typedef struct {
     int column_stride;
     int plain_writes;
     int sampling;
+    int compact;
 } asaga_options;
 
 /* Outcome of asaga_run.  seconds = wall time of the call; solver_seconds and
@@ -162,6 +170,8 @@ typedef struct {
                             float64 scatters                                    */
     int warps_per_block; /* update kernel blocks: 8 warps, or fewer when the
                             autotuner found the warps faster spread over the SMs */
+    int col_index_bytes; /* 4, 2 (compact uint16 indices) or 0 (dense)          */
+    int row_values;      /* 1 when A is held as one value per row (compact)     */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */

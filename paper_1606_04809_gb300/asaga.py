@@ -49,7 +49,7 @@ class asaga_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("epochs_per_segment", ctypes.c_int),
                 ("abar_recompute_every", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("cuda_stream", ctypes.c_void_p), ("column_stride", ctypes.c_int),
-                ("plain_writes", ctypes.c_int), ("sampling", ctypes.c_int)]
+                ("plain_writes", ctypes.c_int), ("sampling", ctypes.c_int), ("compact", ctypes.c_int)]
 
 
 class asaga_result(ctypes.Structure):
@@ -66,7 +66,8 @@ class asaga_info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("d", ctypes.c_int64), ("nnz", ctypes.c_int64), ("L", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("warps", ctypes.c_int),
                 ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
-                ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("warps_per_block", ctypes.c_int)]
+                ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("warps_per_block", ctypes.c_int),
+                ("col_index_bytes", ctypes.c_int), ("row_values", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

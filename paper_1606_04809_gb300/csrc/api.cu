@@ -27,7 +27,8 @@ struct asaga_ctx {
     int64_t n = 0, d = 0, nnz = 0, max_row_len = 0;
     bool dense = false;
     int loss = 0;
-    int vtype = kF32;
+    int vtype = kF32;   // storage type of the values (set-up layout)
+    int layout = kF32;  // layout the steady-state kernels read: vtype or kRowScale, | kIdx16
     double lambda = 0, gamma = 0, L = 0, delta = 0;
     int stride = 1;
     int warps = 1;
@@ -48,8 +49,10 @@ struct asaga_ctx {
 
     // device buffers
     int64_t *row_ptr = nullptr;
-    int32_t *col_idx = nullptr;
-    void *values = nullptr;
+    int32_t *col_idx = nullptr;   // freed once compacted to col16
+    uint16_t *col16 = nullptr;    // compact layout: uint16 column indices (d <= 65536)
+    void *values = nullptr;       // freed once compacted to row_scale
+    float *row_scale = nullptr;   // compact layout: one value per row
     float *lab32 = nullptr;
     double *lab64 = nullptr;
     float *alpha = nullptr;
@@ -77,7 +80,7 @@ struct asaga_batch {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int device = 0;
-    int vtype = kF32;
+    int layout = kF32;  // the instances' common layout (ValType | kIdx16)
     bool dense = false;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -301,13 +304,21 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
     return ASAGA_OK;
 }
 
+// Column indices and values as the steady-state kernels read them.
+const void *layout_cols(const asaga_ctx *c) {
+    return (c->layout & kIdx16) ? (const void *)c->col16 : (const void *)c->col_idx;
+}
+const void *layout_values(const asaga_ctx *c) {
+    return (c->layout & ~kIdx16) == kRowScale ? (const void *)c->row_scale : c->values;
+}
+
 EvalParams eval_params(const asaga_ctx *c) {
     EvalParams e;
     e.n = c->n;
     e.d = c->d;
     e.row_ptr = c->row_ptr;
-    e.col_idx = c->col_idx;
-    e.values = c->values;
+    e.col_idx = layout_cols(c);
+    e.values = layout_values(c);
     e.labels = c->lab64;
     e.alpha = c->alpha;
     e.state = c->state;
@@ -323,7 +334,7 @@ EvalParams eval_params(const asaga_ctx *c) {
 // Launches the float64 objective; result lands in c->dout[0].
 asaga_status enqueue_objective(asaga_ctx *c, std::string *err) {
     const EvalParams e = eval_params(c);
-    CK(launch_objective_rows(e, c->vtype, c->dense, c->eval_grid, c->partial, c->stream), "objective kernel");
+    CK(launch_objective_rows(e, c->layout, c->dense, c->eval_grid, c->partial, c->stream), "objective kernel");
     CK(launch_objective_finish(c->partial, c->eval_grid, 1.0 / (double)c->n, c->lambda, c->dout, c->stream),
        "objective finish");
     c->launches += 2;
@@ -334,7 +345,7 @@ asaga_status enqueue_objective(asaga_ctx *c, std::string *err) {
 asaga_status enqueue_recompute(asaga_ctx *c, std::string *err) {
     const EvalParams e = eval_params(c);
     CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
-    CK(launch_scatter_rows(e, c->vtype, c->dense, 1, c->eval_grid, c->acc64, c->stream), "abar scatter");
+    CK(launch_scatter_rows(e, c->layout, c->dense, 1, c->eval_grid, c->acc64, c->stream), "abar scatter");
     CK(launch_column_finish(e, 1, c->eval_grid, c->acc64, c->partial, c->stream), "abar finish");
     CK(launch_reduce_partials(c->partial, c->eval_grid, 1, c->dout + 1, c->stream), "abar reduce");
     c->launches += 3;
@@ -367,6 +378,56 @@ asaga_status select_hot_columns(asaga_ctx *c, const std::vector<int> &count, std
     CK(cudaMemcpyAsync(c->hot_col, cand.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
        "copy hot columns");
     return stream_sync(c, err);
+}
+
+// Compact layouts of A, applied after the set-up (D, L and the frequent
+// columns are computed on the int32, one-value-per-entry layout).
+// rows_constant: whether every row's stored values are equal (binary rows
+// scaled to unit norm, for instance).
+asaga_status rows_constant(asaga_ctx *c, bool *out, std::string *err) {
+    *out = false;
+    if (c->dense || c->nnz == 0) return ASAGA_OK;
+    int *flag = nullptr;
+    CK(cudaMallocAsync((void **)&flag, sizeof(int), c->stream), "alloc flag");
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), c->stream), "memset flag");
+    CK(launch_row_constant_check(c->row_ptr, c->values, c->vtype, c->n, flag, c->stream), "row check");
+    ++c->launches;
+    CK(cudaMemcpyAsync(c->hstatus, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy flag");
+    CK(cudaFreeAsync(flag, c->stream), "free flag");
+    TRY(stream_sync(c, err));
+    *out = c->hstatus[0] == 0;
+    c->hstatus[0] = 0;
+    return ASAGA_OK;
+}
+
+// rows_equal: keep one float32 value per row (the stored value, exactly)
+// instead of one per entry; idx16: uint16 column indices (d <= 65536).  The
+// arithmetic is unchanged: the kernels see the same numbers.
+asaga_status apply_compact(asaga_ctx *c, bool rows_equal, bool idx16, std::string *err) {
+    if (c->dense || c->nnz == 0) return ASAGA_OK;
+    const size_t vsz = c->vtype == kF32 ? 4 : 2;
+    if (rows_equal) {
+        TRY(dev_alloc(&c->row_scale, c->n, c, err, "alloc row values"));
+        CK(launch_row_scale(c->row_ptr, c->values, c->vtype, c->n, c->row_scale, c->stream), "row values");
+        ++c->launches;
+        TRY(stream_sync(c, err));
+        cudaFree(c->values);
+        c->values = nullptr;
+        c->device_bytes -= (int64_t)(c->nnz * vsz + 64);
+        c->layout = kRowScale;
+    }
+    if (idx16 && c->d <= 65536) {
+        // 64 bytes of slack: the update kernel stages 16-bit indices as aligned 32-bit words
+        TRY(dev_alloc(&c->col16, (size_t)c->nnz + 32, c, err, "alloc 16-bit columns"));
+        CK(launch_cols_to_u16(c->col_idx, c->col16, c->nnz, c->stream), "16-bit columns");
+        ++c->launches;
+        TRY(stream_sync(c, err));
+        cudaFree(c->col_idx);
+        c->col_idx = nullptr;
+        c->device_bytes -= (int64_t)(c->nnz * sizeof(int32_t));
+        c->layout |= kIdx16;
+    }
+    return ASAGA_OK;
 }
 
 asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
@@ -491,10 +552,16 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
         c->delta = (double)mx / (double)c->n;
     }
     if (!c->dense) TRY(select_hot_columns(c, count_h, err));
+    c->layout = c->vtype;
+    if (o->compact && !c->dense) {
+        bool rows_equal = false;
+        TRY(rows_constant(c, &rows_equal, err));
+        TRY(apply_compact(c, rows_equal, c->d <= 65536, err));
+    }
 
     // concurrency: resident warps of the update kernel, bounded by n so that
     // the overlap stays far below n/10 (Theorem 2's condition)
-    const int bps = update_max_blocks_per_sm(c->vtype, c->dense);
+    const int bps = update_max_blocks_per_sm(c->layout, c->dense);
     const int64_t resident = (int64_t)c->sms * bps * (kUpdateBlock / 32);
     int64_t w = o->max_warps > 0 ? o->max_warps : std::max<int64_t>(1, c->n / 64);
     if (w > resident) w = resident;
@@ -510,7 +577,9 @@ void release(asaga_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFree(c->row_ptr);
     cudaFree(c->col_idx);
+    cudaFree(c->col16);
     cudaFree(c->values);
+    cudaFree(c->row_scale);
     cudaFree(c->lab32);
     cudaFree(c->lab64);
     cudaFree(c->alpha);
@@ -537,8 +606,8 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.d = c->d;
     u.nnz = c->nnz;
     u.row_ptr = c->row_ptr;
-    u.col_idx = c->col_idx;
-    u.values = c->values;
+    u.col_idx = layout_cols(c);
+    u.values = layout_values(c);
     u.labels = c->lab32;
     u.alpha = c->alpha;
     u.state = c->state;
@@ -576,7 +645,7 @@ asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
     const int wpb = update_warps_per_block(c, u.nwarps);
     const int block = 32 * wpb;
     const int grid = (u.nwarps + wpb - 1) / wpb;
-    CK(launch_update(u, c->vtype, c->dense, grid, block, c->stream), "update kernel");
+    CK(launch_update(u, c->layout, c->dense, grid, block, c->stream), "update kernel");
     ++c->launches;
     return ASAGA_OK;
 }
@@ -678,7 +747,7 @@ asaga_status reset_state(asaga_ctx *c, std::string *err) {
 asaga_status enqueue_grad(asaga_ctx *c, std::string *err) {
     const EvalParams e = eval_params(c);
     CK(cudaMemsetAsync(c->acc64, 0, c->d * sizeof(double), c->stream), "memset");
-    CK(launch_scatter_rows(e, c->vtype, c->dense, 0, c->eval_grid, c->acc64, c->stream), "gradient scatter");
+    CK(launch_scatter_rows(e, c->layout, c->dense, 0, c->eval_grid, c->acc64, c->stream), "gradient scatter");
     CK(launch_column_finish(e, 0, c->eval_grid, c->acc64, c->partial, c->stream), "gradient finish");
     CK(launch_reduce_partials(c->partial, c->eval_grid, 0, c->dout + 2, c->stream), "gradient reduce");
     c->launches += 3;
@@ -1180,6 +1249,7 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
     for (int i = 0; i < count; ++i) {
         asaga_options o = options[i];
         o.cuda_stream = b->stream;
+        o.compact = 0;  // decided below for all instances together (one kernel layout)
         asaga_ctx *c = new (std::nothrow) asaga_ctx();
         if (!c) return fail(err, ASAGA_ENOMEM, "host allocation failed");
         std::string e;
@@ -1190,13 +1260,23 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
         }
         b->ctx.push_back(c);
     }
-    b->vtype = b->ctx[0]->vtype;
+    if (options[0].compact && !b->ctx[0]->dense) {
+        bool all_equal = true, all_small = true;
+        for (auto *c : b->ctx) {
+            bool eq = false;
+            TRY(rows_constant(c, &eq, err));
+            all_equal = all_equal && eq;
+            all_small = all_small && c->d <= 65536;
+        }
+        for (auto *c : b->ctx) TRY(apply_compact(c, all_equal, all_small, err));
+    }
+    b->layout = b->ctx[0]->layout;
     b->dense = b->ctx[0]->dense;
     b->epochs_per_segment = std::max(1, options[0].epochs_per_segment);
     b->abar_every = options[0].abar_recompute_every;
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, b->device), "cudaGetDeviceProperties");
-    b->resident_blocks = prop.multiProcessorCount * batch_update_max_blocks_per_sm(b->vtype, b->dense);
+    b->resident_blocks = prop.multiProcessorCount * batch_update_max_blocks_per_sm(b->layout, b->dense);
     b->eval_grid = std::max(1, std::min(64, (prop.multiProcessorCount * 8 + count - 1) / count));
     CK(cudaMallocHost((void **)&b->h_up, count * sizeof(UpdateParams)), "alloc pinned");
     CK(cudaMallocHost((void **)&b->h_f, count * sizeof(double)), "alloc pinned");
@@ -1223,9 +1303,9 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
 asaga_status batch_enqueue_segment(asaga_batch *b, std::string *err) {
     CK(cudaMemcpyAsync(b->d_up, b->h_up, b->count * sizeof(UpdateParams), cudaMemcpyHostToDevice, b->stream),
        "copy params");
-    CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->vtype, b->dense, b->stream),
+    CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->layout, b->dense, b->stream),
        "batch update kernel");
-    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->vtype, b->dense, b->d_partial, b->d_f, b->stream),
+    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->layout, b->dense, b->d_partial, b->d_f, b->stream),
        "batch objective");
     CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
     return ASAGA_OK;
@@ -1457,6 +1537,7 @@ void asaga_default_options(asaga_options *o) {
     o->column_stride = 0;
     o->plain_writes = 0;
     o->sampling = ASAGA_SAMPLE_UNIFORM;
+    o->compact = 0;
 }
 
 asaga_status asaga_create(asaga_ctx **out, const asaga_problem *p, const asaga_options *o) {
@@ -1605,6 +1686,8 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->max_row_len = c->max_row_len;
     info->n_hot = c->n_hot;
     info->warps_per_block = update_warps_per_block(c, c->warps);
+    info->col_index_bytes = c->dense ? 0 : ((c->layout & kIdx16) ? 2 : 4);
+    info->row_values = (c->layout & ~kIdx16) == kRowScale ? 1 : 0;
     return ASAGA_OK;
 }
 
@@ -1696,7 +1779,7 @@ asaga_status asaga_batch_objective(asaga_batch *b, double *f) {
     if (!b || !f) return ASAGA_EINVAL;
     std::string *err = &b->err;
     CK(cudaSetDevice(b->device), "cudaSetDevice");
-    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->vtype, b->dense, b->d_partial, b->d_f, b->stream),
+    CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->layout, b->dense, b->d_partial, b->d_f, b->stream),
        "batch objective");
     CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
     CK(cudaStreamSynchronize(b->stream), "sync");

@@ -9,8 +9,13 @@
 
 namespace asaga {
 
-// Device element type of A's values.
-enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3 };
+// Device element type of A's values; kRowScale: one float32 value per row
+// (every stored value of the row is equal, e.g. binary rows scaled to unit
+// norm), held in the `values` array of n entries.
+enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3, kRowScale = 4 };
+// A layout, as the steady-state kernels see A: a ValType, or'ed with
+// kIdx16 when the column indices are stored as uint16 (d <= 65536).
+constexpr int kIdx16 = 8;
 
 // Per-column solver state, 16 bytes: the iterate x_v, the running average
 // abar_v and the reweighting D_v, gathered by one 16-byte load and updated
@@ -25,8 +30,8 @@ struct UpdateParams {
     int64_t n, d;
     int64_t nnz;              // entries of A (n*d for dense); staged row ranges are checked against it
     const int64_t *row_ptr;   // n+1 (sparse) or nullptr (dense)
-    const int32_t *col_idx;   // nnz (sparse) or nullptr (dense)
-    const void *values;       // nnz (or n*d) of the storage type
+    const void *col_idx;      // nnz int32 or uint16 (by layout), or nullptr (dense)
+    const void *values;       // nnz (or n*d) of the storage type, or n row values (kRowScale)
     const float *labels;      // n, float32 copy for the update
     float *alpha;             // n, scalar memory per sample
     float4 *state;            // d * stride
@@ -50,8 +55,8 @@ struct UpdateParams {
 struct EvalParams {
     int64_t n, d;
     const int64_t *row_ptr;
-    const int32_t *col_idx;
-    const void *values;
+    const void *col_idx;      // int32 or uint16 by layout (int32 in the set-up kernels)
+    const void *values;       // per entry, or per row (kRowScale)
     const double *labels;     // n, float64
     const float *alpha;       // n
     float4 *state;
@@ -76,28 +81,28 @@ void set_thread_error(const std::string &msg);
 // rows[j] = the row of update t_begin + j (device buffer of count entries)
 cudaError_t launch_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
                                int64_t *rows, cudaStream_t stream);
-cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
+cudaError_t launch_update(const UpdateParams &p, int layout, bool dense, int grid, int block,
                           cudaStream_t s);
-int update_max_blocks_per_sm(int vtype, bool dense);
+int update_max_blocks_per_sm(int layout, bool dense);
 // params[count] and block_begin[count] in device memory; instance i owns blocks
 // [block_begin[i], block_begin[i+1]) (the last one up to grid).
-cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int vtype,
+cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int layout,
                                 bool dense, cudaStream_t s);
-int batch_update_max_blocks_per_sm(int vtype, bool dense);
+int batch_update_max_blocks_per_sm(int layout, bool dense);
 
 // eval.cu
 // partial[0..grid) <- per-block sums of phi_i(a_i.x); partial[grid..2grid) <- sums of x_v^2.
-cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, int grid,
+cudaError_t launch_objective_rows(const EvalParams &p, int layout, bool dense, int grid,
                                   double *partial, cudaStream_t s);
 // out[0] <- (sum partial[0..grid))/n + lambda/2 (sum partial[grid..2grid)).
 cudaError_t launch_objective_finish(const double *partial, int grid, double inv_n, double lambda,
                                     double *out, cudaStream_t s);
 // Objectives of `count` instances in one launch of grid x count blocks:
 // partial holds 2 * grid * count doubles; f_out[i] receives instance i's f.
-cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int vtype, bool dense,
+cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int layout, bool dense,
                                    double *partial, double *f_out, cudaStream_t s);
 // acc[v] += sum_i w_i a_iv with w_i = phi'_i(a_i.x)/n (mode 0) or alpha_i/n (mode 1).
-cudaError_t launch_scatter_rows(const EvalParams &p, int vtype, bool dense, int mode, int grid,
+cudaError_t launch_scatter_rows(const EvalParams &p, int layout, bool dense, int mode, int grid,
                                 double *acc, cudaStream_t s);
 // mode 0 (gradient): acc[v] += lambda x_v; partial[b] <- block sums of acc[v]^2.
 // mode 1 (abar):     partial[b] <- block max |abar_v - acc[v]|, then abar_v <- (float)acc[v].
@@ -113,12 +118,20 @@ cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count
 cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n,
                               cudaStream_t s);
 // out[0] <- max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) (float64) over the stored
-// values; needs D in state.z.
+// values; needs D in state.z.  Set-up layout: int32 columns, one value per entry.
 cudaError_t launch_max_row_smoothness(const EvalParams &p, int vtype, bool dense, double c_loss, int grid,
                                       double *partial, double *out, cudaStream_t s);
 // dst (vtype) <- src (src_dtype: 0 f64, 1 f32, 2 bf16, 3 f16), count elements.
 cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype, int64_t count,
                            cudaStream_t s);
 cudaError_t launch_labels(const double *lab64, float *lab32, int64_t n, cudaStream_t s);
+// Compact layouts (set-up): flag[0] |= 1 if some row holds two different
+// stored values (vtype, per-entry values); scale[i] <- the value of row i
+// (0 for an empty row); col16[k] <- col[k].
+cudaError_t launch_row_constant_check(const int64_t *row_ptr, const void *values, int vtype, int64_t n, int *flag,
+                                      cudaStream_t s);
+cudaError_t launch_row_scale(const int64_t *row_ptr, const void *values, int vtype, int64_t n, float *scale,
+                             cudaStream_t s);
+cudaError_t launch_cols_to_u16(const int32_t *col, uint16_t *col16, int64_t nnz, cudaStream_t s);
 
 }  // namespace asaga

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "asaga_internal.h"
+
 namespace asaga {
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -18,6 +20,58 @@ template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return _
 // Streaming read of A (each row is read once per visit; evict-first so that
 // the solver state keeps the L2).
 template <typename T> __device__ __forceinline__ T ld_stream(const T *p) { return __ldcs(p); }
+
+// ---- layouts of A in the steady-state kernels --------------------------
+// Values: float / bf16 / half per entry, or RowScale (one float per row).
+// Column indices: int32_t or uint16_t (d <= 65536).
+struct RowScale {};
+template <typename T> struct IsRowScale { static constexpr bool value = false; };
+template <> struct IsRowScale<RowScale> { static constexpr bool value = true; };
+
+// Column index of entry k, read-only path / streaming path.
+template <typename I> __device__ __forceinline__ int col_ro(const void *col, int64_t k) {
+    return (int)__ldg(static_cast<const I *>(col) + k);
+}
+template <typename I> __device__ __forceinline__ int col_stream(const void *col, int64_t k) {
+    return (int)__ldcs(static_cast<const I *>(col) + k);
+}
+// Value of entry k of row i.
+template <typename T> __device__ __forceinline__ float value_at(const void *values, int64_t i, int64_t k) {
+    if constexpr (IsRowScale<T>::value)
+        return static_cast<const float *>(values)[i];
+    else
+        return to_f32(static_cast<const T *>(values)[k]);
+}
+
+// Calls f.template run<T, I, kDense>() for a layout (ValType | kIdx16);
+// returns `bad` for a layout without kernels.
+template <typename R, typename F> R with_layout(int layout, bool dense, F &&f, R bad) {
+    const int v = layout & ~kIdx16;
+    if (dense) {
+        switch (v) {
+        case kF32: return f.template run<float, int32_t, true>();
+        case kBF16: return f.template run<__nv_bfloat16, int32_t, true>();
+        case kF16: return f.template run<__half, int32_t, true>();
+        default: return bad;
+        }
+    }
+    if (layout & kIdx16) {
+        switch (v) {
+        case kF32: return f.template run<float, uint16_t, false>();
+        case kBF16: return f.template run<__nv_bfloat16, uint16_t, false>();
+        case kF16: return f.template run<__half, uint16_t, false>();
+        case kRowScale: return f.template run<RowScale, uint16_t, false>();
+        default: return bad;
+        }
+    }
+    switch (v) {
+    case kF32: return f.template run<float, int32_t, false>();
+    case kBF16: return f.template run<__nv_bfloat16, int32_t, false>();
+    case kF16: return f.template run<__half, int32_t, false>();
+    case kRowScale: return f.template run<RowScale, int32_t, false>();
+    default: return bad;
+    }
+}
 
 // Read of shared state at L2 (bypasses L1, which is not coherent with the
 // atomics other SMs apply).

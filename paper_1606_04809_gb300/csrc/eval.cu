@@ -49,14 +49,13 @@ __device__ __forceinline__ double ff_value(const FF &a) { return (double)a.hi + 
 
 // z_i = a_i . x for one row, by one thread (rows are split over threads so
 // that the float64 work per row runs on all 32 lanes at once).
-template <typename T>
-__device__ __forceinline__ double row_dot_thread(const EvalParams &P, const T *vals, int64_t start, int len,
-                                                 bool dense) {
+template <typename T, typename I>
+__device__ __forceinline__ double row_dot_thread(const EvalParams &P, int64_t i, int64_t start, int len, bool dense) {
     FF acc;
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
-        const int c = dense ? k : __ldg(P.col_idx + start + k);
-        ff_add_product(acc, to_f32(vals[start + k]), ld_state_ro(P.state + (int64_t)c * P.stride).x);
+        const int c = dense ? k : col_ro<I>(P.col_idx, start + k);
+        ff_add_product(acc, value_at<T>(P.values, i, start + k), ld_state_ro(P.state + (int64_t)c * P.stride).x);
     }
     return ff_value(acc);
 }
@@ -89,15 +88,14 @@ __device__ __forceinline__ double block_reduce(double v, bool is_max) {
     return r;  // valid in thread 0
 }
 
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalParams P, double *partial) {
-    const T *vals = static_cast<const T *>(P.values);
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t start;
         int len;
         row_range<T, kDense>(P, i, start, len);
-        const double z = row_dot_thread<T>(P, vals, start, len, kDense);
+        const double z = row_dot_thread<T, I>(P, i, start, len, kDense);
         acc += phi_f64(P.loss, z, P.labels[i]);
     }
     double xx = 0.0;
@@ -115,19 +113,18 @@ __global__ void __launch_bounds__(kEvalBlock) objective_rows_kernel(const EvalPa
 
 // The objective of many instances in one launch: blockIdx.y = instance,
 // blockIdx.x = one of gridDim.x blocks over that instance's rows.
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __global__ void __launch_bounds__(kEvalBlock) batch_objective_rows_kernel(const EvalParams *__restrict__ params,
                                                                           double *partial) {
     __shared__ EvalParams sp;
     if (threadIdx.x == 0) sp = params[blockIdx.y];
     __syncthreads();
-    const T *vals = static_cast<const T *>(sp.values);
     double acc = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < sp.n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t start;
         int len;
         row_range<T, kDense>(sp, i, start, len);
-        acc += phi_f64(sp.loss, row_dot_thread<T>(sp, vals, start, len, kDense), sp.labels[i]);
+        acc += phi_f64(sp.loss, row_dot_thread<T, I>(sp, i, start, len, kDense), sp.labels[i]);
     }
     double xx = 0.0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < sp.d; v += (int64_t)gridDim.x * blockDim.x) {
@@ -177,10 +174,9 @@ __global__ void objective_finish_kernel(const double *partial, int grid, double 
 //         1 = dense rows, all d columns accumulate per block in shared memory;
 //         2 = the n_hot most frequent columns accumulate per block in shared
 //             memory (their atomics would otherwise serialise at one L2 line).
-template <typename T, bool kDense, int kSlotsMode>
+template <typename T, typename I, bool kDense, int kSlotsMode>
 __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalParams P, int mode, double *acc) {
     extern __shared__ double sacc[];
-    const T *vals = static_cast<const T *>(P.values);
     const double inv_n = 1.0 / (double)P.n;
     const int nslots = kSlotsMode == 1 ? (int)P.d : (kSlotsMode == 2 ? P.n_hot : 0);
     if (kSlotsMode) {
@@ -193,15 +189,15 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
         row_range<T, kDense>(P, i, start, len);
         double w;
         if (mode == 0) {
-            const double z = row_dot_thread<T>(P, vals, start, len, kDense);
+            const double z = row_dot_thread<T, I>(P, i, start, len, kDense);
             w = phi_prime_f64(P.loss, z, P.labels[i]) * inv_n;
         } else {
             w = (double)P.alpha[i] * inv_n;
         }
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
-            const int c = kDense ? k : __ldg(P.col_idx + start + k);
-            const double contrib = w * (double)to_f32(vals[start + k]);
+            const int c = kDense ? k : col_ro<I>(P.col_idx, start + k);
+            const double contrib = w * (double)value_at<T>(P.values, i, start + k);
             const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);
             if (slot >= 0)
                 atomicAdd(sacc + slot, contrib);
@@ -277,7 +273,7 @@ __global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalPa
         for (int k = lane; k < len; k += 32) {
             const double a = (double)to_f32(vals[start + k]);
             s += a * a;
-            const int c = kDense ? k : P.col_idx[start + k];
+            const int c = kDense ? k : static_cast<const int32_t *>(P.col_idx)[start + k];
             dmax = fmax(dmax, (double)ld_state_ro(P.state + (int64_t)c * P.stride).z);
         }
         best = fmax(best, c_loss * warp_sum(s) + P.lambda * warp_max(dmax));
@@ -323,36 +319,36 @@ static int elementwise_grid(int64_t count) {
     return g < 1 ? 1 : (int)g;
 }
 
-template <typename T, bool kDense>
-static void objective_rows_t(const EvalParams &p, int grid, double *partial, cudaStream_t s) {
-    objective_rows_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, partial);
-}
+struct ObjectiveRows {
+    const EvalParams &p;
+    int grid;
+    double *partial;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        objective_rows_kernel<T, I, kDense><<<grid, kEvalBlock, 0, s>>>(p, partial);
+        return cudaGetLastError();
+    }
+};
 
-cudaError_t launch_objective_rows(const EvalParams &p, int vtype, bool dense, int grid, double *partial,
+cudaError_t launch_objective_rows(const EvalParams &p, int layout, bool dense, int grid, double *partial,
                                   cudaStream_t s) {
-    switch (vtype) {
-    case kF32: dense ? objective_rows_t<float, true>(p, grid, partial, s) : objective_rows_t<float, false>(p, grid, partial, s); break;
-    case kBF16: dense ? objective_rows_t<__nv_bfloat16, true>(p, grid, partial, s) : objective_rows_t<__nv_bfloat16, false>(p, grid, partial, s); break;
-    case kF16: dense ? objective_rows_t<__half, true>(p, grid, partial, s) : objective_rows_t<__half, false>(p, grid, partial, s); break;
-    default: return cudaErrorInvalidValue;
+    return with_layout(layout, dense, ObjectiveRows{p, grid, partial, s}, cudaErrorInvalidValue);
+}
+
+struct BatchObjective {
+    const EvalParams *params;
+    int count, grid;
+    double *partial;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        batch_objective_rows_kernel<T, I, kDense><<<dim3(grid, count), kEvalBlock, 0, s>>>(params, partial);
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
-}
+};
 
-template <typename T, bool kDense>
-static void batch_objective_t(const EvalParams *params, int count, int grid, double *partial, cudaStream_t s) {
-    batch_objective_rows_kernel<T, kDense><<<dim3(grid, count), kEvalBlock, 0, s>>>(params, partial);
-}
-
-cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int vtype, bool dense,
+cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid, int layout, bool dense,
                                    double *partial, double *f_out, cudaStream_t s) {
-    switch (vtype) {
-    case kF32: dense ? batch_objective_t<float, true>(params, count, grid, partial, s) : batch_objective_t<float, false>(params, count, grid, partial, s); break;
-    case kBF16: dense ? batch_objective_t<__nv_bfloat16, true>(params, count, grid, partial, s) : batch_objective_t<__nv_bfloat16, false>(params, count, grid, partial, s); break;
-    case kF16: dense ? batch_objective_t<__half, true>(params, count, grid, partial, s) : batch_objective_t<__half, false>(params, count, grid, partial, s); break;
-    default: return cudaErrorInvalidValue;
-    }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = with_layout(layout, dense, BatchObjective{params, count, grid, partial, s}, cudaErrorInvalidValue);
     if (e != cudaSuccess) return e;
     batch_objective_finish_kernel<<<count, 256, 0, s>>>(params, partial, grid, f_out);
     return cudaGetLastError();
@@ -364,26 +360,27 @@ cudaError_t launch_objective_finish(const double *partial, int grid, double inv_
     return cudaGetLastError();
 }
 
-template <typename T, bool kDense>
-static cudaError_t scatter_t(const EvalParams &p, int mode, int grid, double *acc, cudaStream_t s) {
-    if (kDense && p.d <= kSmemCols) {
-        scatter_rows_kernel<T, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
-    } else if (!kDense && p.n_hot > 0 && p.hot_slot) {
-        scatter_rows_kernel<T, kDense, 2><<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, mode, acc);
-    } else {
-        scatter_rows_kernel<T, kDense, 0><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
+struct ScatterRows {
+    const EvalParams &p;
+    int mode, grid;
+    double *acc;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        if (kDense && p.d <= kSmemCols) {
+            scatter_rows_kernel<T, I, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
+        } else if (!kDense && p.n_hot > 0 && p.hot_slot) {
+            scatter_rows_kernel<T, I, kDense, 2><<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, mode,
+                                                                                                           acc);
+        } else {
+            scatter_rows_kernel<T, I, kDense, 0><<<grid, kEvalBlock, 0, s>>>(p, mode, acc);
+        }
+        return cudaGetLastError();
     }
-    return cudaGetLastError();
-}
+};
 
-cudaError_t launch_scatter_rows(const EvalParams &p, int vtype, bool dense, int mode, int grid, double *acc,
+cudaError_t launch_scatter_rows(const EvalParams &p, int layout, bool dense, int mode, int grid, double *acc,
                                 cudaStream_t s) {
-    switch (vtype) {
-    case kF32: return dense ? scatter_t<float, true>(p, mode, grid, acc, s) : scatter_t<float, false>(p, mode, grid, acc, s);
-    case kBF16: return dense ? scatter_t<__nv_bfloat16, true>(p, mode, grid, acc, s) : scatter_t<__nv_bfloat16, false>(p, mode, grid, acc, s);
-    case kF16: return dense ? scatter_t<__half, true>(p, mode, grid, acc, s) : scatter_t<__half, false>(p, mode, grid, acc, s);
-    default: return cudaErrorInvalidValue;
-    }
+    return with_layout(layout, dense, ScatterRows{p, mode, grid, acc, s}, cudaErrorInvalidValue);
 }
 
 cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double *acc, double *partial,
@@ -450,6 +447,63 @@ cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype,
 
 cudaError_t launch_labels(const double *lab64, float *lab32, int64_t n, cudaStream_t s) {
     labels_kernel<<<elementwise_grid(n), 256, 0, s>>>(lab64, lab32, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ compact layouts
+
+// flag[0] |= 1 when a row holds two different stored values.
+template <typename T>
+__global__ void row_constant_kernel(const int64_t *row_ptr, const T *vals, int64_t n, int *flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr[i], b = row_ptr[i + 1];
+        if (b <= a) continue;
+        const float v0 = to_f32(vals[a]);
+        for (int64_t k = a + 1; k < b; ++k)
+            if (to_f32(vals[k]) != v0) {
+                atomicOr(flag, 1);
+                break;
+            }
+    }
+}
+
+template <typename T>
+__global__ void row_scale_kernel(const int64_t *row_ptr, const T *vals, int64_t n, float *scale) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        scale[i] = row_ptr[i + 1] > row_ptr[i] ? to_f32(vals[row_ptr[i]]) : 0.f;
+}
+
+__global__ void cols_to_u16_kernel(const int32_t *col, uint16_t *col16, int64_t nnz) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        col16[k] = (uint16_t)col[k];
+}
+
+cudaError_t launch_row_constant_check(const int64_t *row_ptr, const void *values, int vtype, int64_t n, int *flag,
+                                      cudaStream_t s) {
+    const int g = elementwise_grid(n);
+    switch (vtype) {
+    case kF32: row_constant_kernel<float><<<g, 256, 0, s>>>(row_ptr, (const float *)values, n, flag); break;
+    case kBF16: row_constant_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(row_ptr, (const __nv_bfloat16 *)values, n, flag); break;
+    case kF16: row_constant_kernel<__half><<<g, 256, 0, s>>>(row_ptr, (const __half *)values, n, flag); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_scale(const int64_t *row_ptr, const void *values, int vtype, int64_t n, float *scale,
+                             cudaStream_t s) {
+    const int g = elementwise_grid(n);
+    switch (vtype) {
+    case kF32: row_scale_kernel<float><<<g, 256, 0, s>>>(row_ptr, (const float *)values, n, scale); break;
+    case kBF16: row_scale_kernel<__nv_bfloat16><<<g, 256, 0, s>>>(row_ptr, (const __nv_bfloat16 *)values, n, scale); break;
+    case kF16: row_scale_kernel<__half><<<g, 256, 0, s>>>(row_ptr, (const __half *)values, n, scale); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_to_u16(const int32_t *col, uint16_t *col16, int64_t nnz, cudaStream_t s) {
+    if (nnz > 0) cols_to_u16_kernel<<<elementwise_grid(nnz), 256, 0, s>>>(col, col16, nnz);
     return cudaGetLastError();
 }
 

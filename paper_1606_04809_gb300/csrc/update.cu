@@ -49,7 +49,8 @@ struct __align__(16) WarpRing {
     int64_t end[kMetaRing];    // row_ptr[i + 1]
     int64_t row[kMetaRing];    // i, or -1 past the end
     float label[kMetaRing];
-    int32_t col[kStages][kRowCap];
+    float scale[kMetaRing];    // the row's value (RowScale layout)
+    int32_t col[kStages][kRowCap];  // int32 indices, or pairs of uint16 indices as aligned 32-bit words
     uint32_t val[kStages][kRowCap];  // raw 32-bit words: one fp32 or two 16-bit values
 };
 
@@ -85,6 +86,16 @@ template <> __device__ __forceinline__ float staged_value<__half>(const uint32_t
     return __half2float(__ushort_as_half(h));
 }
 
+// Column of staged entry k: int32 words, or uint16 halves of aligned 32-bit
+// words starting at the word that holds entry `start`.
+template <typename I> __device__ __forceinline__ int staged_col(const int32_t *words, int64_t start, int k);
+template <> __device__ __forceinline__ int staged_col<int32_t>(const int32_t *words, int64_t, int k) {
+    return words[k];
+}
+template <> __device__ __forceinline__ int staged_col<uint16_t>(const int32_t *words, int64_t start, int k) {
+    return reinterpret_cast<const uint16_t *>(words)[(int)(start & 1) + k];
+}
+
 // Row of update t of this launch, or -1 past the end (or on a bad index).
 __device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool &bad) {
     if (t >= P.count) return -1;
@@ -100,7 +111,7 @@ __device__ __forceinline__ int64_t row_of(const UpdateParams &P, int64_t t, bool
 }
 
 // Lane 0 requests row i's row_ptr entries and label into meta slot m.
-template <bool kDense>
+template <typename T, bool kDense>
 __device__ __forceinline__ void stage_meta(const UpdateParams &P, WarpRing &R, int m, int64_t i, int lane) {
     if (lane != 0) return;
     R.row[m] = i;
@@ -113,11 +124,13 @@ __device__ __forceinline__ void stage_meta(const UpdateParams &P, WarpRing &R, i
         cp_async8(&R.end[m], P.row_ptr + i + 1);
     }
     cp_async4(&R.label[m], P.labels + i);
+    if constexpr (IsRowScale<T>::value) cp_async4(&R.scale[m], static_cast<const float *>(P.values) + i);
 }
 
 // All lanes request the first kRowCap column indices and values of the row in
-// meta slot m into stage st (16-bit values travel as aligned 32-bit words).
-template <typename T, bool kDense>
+// meta slot m into stage st (16-bit values and indices travel as aligned
+// 32-bit words; a RowScale row has no values to stage).
+template <typename T, typename I, bool kDense>
 __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, int m, int st, int lane) {
     if (R.row[m] < 0) return;
     const int64_t start = R.start[m];
@@ -128,9 +141,19 @@ __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, 
     }
     const int len = (int)(end - start);
     const int cnt = len < kRowCap ? len : kRowCap;
-    if (!kDense)
-        for (int j = lane; j < cnt; j += 32) cp_async4(&R.col[st][j], P.col_idx + start + j);
-    if (sizeof(T) == 4) {
+    if (!kDense) {
+        const uint32_t *w = static_cast<const uint32_t *>(P.col_idx);
+        if (sizeof(I) == 4) {
+            for (int j = lane; j < cnt; j += 32) cp_async4(&R.col[st][j], w + start + j);
+        } else {
+            const int64_t w0 = start >> 1;
+            const int nw = (int)(((start + cnt + 1) >> 1) - w0);
+            for (int j = lane; j < nw; j += 32) cp_async4(&R.col[st][j], w + w0 + j);
+        }
+    }
+    if constexpr (IsRowScale<T>::value) {
+        return;
+    } else if (sizeof(T) == 4) {
         const uint32_t *w = static_cast<const uint32_t *>(P.values);
         for (int j = lane; j < cnt; j += 32) cp_async4(&R.val[st][j], w + start + j);
     } else {
@@ -147,14 +170,14 @@ __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, 
 template <bool kDense> struct Update {
     int64_t i, start;
     int len;
-    float label, alpha_hat;
+    float label, alpha_hat, scale;
     int c[kSlots];
     float a[kSlots];
     float4 s[kSlots];
 };
 
 // Reads the staged row and issues the inconsistent reads of x^, abar, D and alpha^_i.
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRing &R, int m, int st, int lane,
                                              Update<kDense> &u) {
     u.i = R.row[m];
@@ -163,6 +186,7 @@ __device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRi
     if (u.start < 0 || end < u.start || end > P.nnz) return false;  // recorded when it was staged
     u.len = (int)(end - u.start);
     u.label = R.label[m];
+    u.scale = IsRowScale<T>::value ? R.scale[m] : 0.f;
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) {
         const int k = lane + 32 * q;
@@ -170,8 +194,11 @@ __device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRi
         u.a[q] = 0.f;
         u.s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < u.len) {
-            u.c[q] = kDense ? k : R.col[st][k];
-            u.a[q] = staged_value<T>(R.val[st], u.start, k);
+            u.c[q] = kDense ? k : staged_col<I>(R.col[st], u.start, k);
+            if constexpr (IsRowScale<T>::value)
+                u.a[q] = u.scale;
+            else
+                u.a[q] = staged_value<T>(R.val[st], u.start, k);
             u.s[q] = ld_state(P.state + u.c[q] * (int64_t)P.stride);
         }
     }
@@ -180,17 +207,29 @@ __device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRi
 }
 
 // Dot product, loss derivative and the atomic adds to x, abar and alpha_i.
-template <typename T, bool kDense>
+// Column and value of entry k >= kRowCap of the update's row (global memory).
+template <typename T, typename I, bool kDense>
+__device__ __forceinline__ void tail_entry(const UpdateParams &P, const Update<kDense> &u, int k, int &col,
+                                          float &a) {
+    col = kDense ? k : col_stream<I>(P.col_idx, u.start + k);
+    if constexpr (IsRowScale<T>::value)
+        a = u.scale;
+    else
+        a = to_f32(ld_stream(static_cast<const T *>(P.values) + u.start + k));
+}
+
+template <typename T, typename I, bool kDense>
 __device__ __forceinline__ void finish_update(const UpdateParams &P, const Update<kDense> &u, int lane) {
-    const T *__restrict__ vals = static_cast<const T *>(P.values);
     const float4 *__restrict__ state = P.state;
     const int64_t stride = P.stride;
     float z = 0.f;
 #pragma unroll
     for (int q = 0; q < kSlots; ++q) z = fmaf(u.a[q], u.s[q].x, z);
     for (int k = lane + kRowCap; k < u.len; k += 32) {  // rest of a long row
-        const int cc = kDense ? k : ld_stream(P.col_idx + u.start + k);
-        z = fmaf(to_f32(ld_stream(vals + u.start + k)), ld_state(state + cc * stride).x, z);
+        int cc;
+        float av;
+        tail_entry<T, I, kDense>(P, u, k, cc, av);
+        z = fmaf(av, ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
     const float delta = phi_prime_f32(P.loss, z, u.label) - u.alpha_hat;  // same value in every lane
@@ -217,8 +256,9 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
         }
     }
     for (int k = lane + kRowCap; k < u.len; k += 32) {
-        const int cc = kDense ? k : ld_stream(P.col_idx + u.start + k);
-        const float av = to_f32(ld_stream(vals + u.start + k));
+        int cc;
+        float av;
+        tail_entry<T, I, kDense>(P, u, k, cc, av);
         const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
         red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
@@ -230,7 +270,7 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
 // Iteration k processes the row of update warp + k W; before it, all commit
 // groups but the newest are complete, which covers that row's staged slice
 // and the row_ptr entries of row k + 2, whose slice is requested next.
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R, int warp, int lane) {
     const int64_t W = P.nwarps;
     uint64_t deadline = 0;
@@ -240,12 +280,12 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
     }
     bool bad = false;
     // prologue: row_ptr entries of rows 0..3, then the slices of rows 0 and 1
-    for (int k = 0; k < 4; ++k) stage_meta<kDense>(P, R, k, row_of(P, warp + k * W, bad), lane);
+    for (int k = 0; k < 4; ++k) stage_meta<T, kDense>(P, R, k, row_of(P, warp + k * W, bad), lane);
     cp_async_wait_all();
     __syncwarp();
-    stage_slice<T, kDense>(P, R, 0, 0, lane);
+    stage_slice<T, I, kDense>(P, R, 0, 0, lane);
     cp_async_commit();
-    stage_slice<T, kDense>(P, R, 1, 1, lane);
+    stage_slice<T, I, kDense>(P, R, 1, 1, lane);
     cp_async_commit();
     int64_t done = 0;
     for (int64_t k = 0;; ++k) {
@@ -257,15 +297,16 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
         // touching the state: the window between this update's reads and
         // writes (which sets the overlap tau) then holds no staging work
         const int m2 = (int)((k + 2) & (kMetaRing - 1));
-        stage_slice<T, kDense>(P, R, m2, (int)((k + 2) & (kStages - 1)), lane);
+        stage_slice<T, I, kDense>(P, R, m2, (int)((k + 2) & (kStages - 1)), lane);
         const bool more = R.row[(k + 3) & (kMetaRing - 1)] >= 0;
-        stage_meta<kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
+        stage_meta<T, kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
                            lane);
         cp_async_commit();
         uint64_t t_read = 0;
         if (P.trace) t_read = globaltimer_ns();
         Update<kDense> u;
-        if (begin_update<T, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u)) finish_update<T, kDense>(P, u, lane);
+        if (begin_update<T, I, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u))
+            finish_update<T, I, kDense>(P, u, lane);
         if (P.trace && lane == 0) {
             P.trace[2 * (warp + k * W)] = t_read;
             P.trace[2 * (warp + k * W) + 1] = globaltimer_ns();
@@ -286,19 +327,19 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
     if (bad && lane == 0) atomicOr(P.status, 2);
 }
 
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams P) {
     __shared__ WarpRing rings[kUpdateBlock / 32];
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= P.nwarps) return;
-    warp_updates<T, kDense>(P, rings[threadIdx.x >> 5], warp, lane);
+    warp_updates<T, I, kDense>(P, rings[threadIdx.x >> 5], warp, lane);
 }
 
 // Many independent problems in one launch: block b serves instance
 // inst = the last i with block_begin[i] <= b, whose parameters are copied to
 // shared memory once; its warps split that instance's updates.
-template <typename T, bool kDense>
+template <typename T, typename I, bool kDense>
 __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateParams *__restrict__ params,
                                                                    const int *__restrict__ block_begin, int count) {
     __shared__ UpdateParams sp;
@@ -317,85 +358,54 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((blockIdx.x - block_begin[s_inst]) * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= sp.nwarps || sp.count <= 0) return;
-    warp_updates<T, kDense>(sp, rings[threadIdx.x >> 5], warp, lane);
+    warp_updates<T, I, kDense>(sp, rings[threadIdx.x >> 5], warp, lane);
 }
 
-template <typename T, bool kDense>
-static cudaError_t launch_t(const UpdateParams &p, int grid, int block, cudaStream_t s) {
-    update_kernel<T, kDense><<<grid, block, 0, s>>>(p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_update(const UpdateParams &p, int vtype, bool dense, int grid, int block,
-                          cudaStream_t s) {
-    switch (vtype) {
-    case kF32: return dense ? launch_t<float, true>(p, grid, block, s) : launch_t<float, false>(p, grid, block, s);
-    case kBF16:
-        return dense ? launch_t<__nv_bfloat16, true>(p, grid, block, s)
-                     : launch_t<__nv_bfloat16, false>(p, grid, block, s);
-    case kF16: return dense ? launch_t<__half, true>(p, grid, block, s) : launch_t<__half, false>(p, grid, block, s);
-    default: return cudaErrorInvalidValue;
+struct UpdateLaunch {
+    const UpdateParams &p;
+    int grid, block;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        update_kernel<T, I, kDense><<<grid, block, 0, s>>>(p);
+        return cudaGetLastError();
     }
+};
+
+cudaError_t launch_update(const UpdateParams &p, int layout, bool dense, int grid, int block, cudaStream_t s) {
+    return with_layout(layout, dense, UpdateLaunch{p, grid, block, s}, cudaErrorInvalidValue);
 }
 
-template <typename T, bool kDense>
-static cudaError_t batch_launch_t(const UpdateParams *params, const int *block_begin, int count, int grid,
-                                  cudaStream_t s) {
-    batch_update_kernel<T, kDense><<<grid, kBatchBlock, 0, s>>>(params, block_begin, count);
-    return cudaGetLastError();
-}
+struct BatchUpdateLaunch {
+    const UpdateParams *params;
+    const int *block_begin;
+    int count, grid;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        batch_update_kernel<T, I, kDense><<<grid, kBatchBlock, 0, s>>>(params, block_begin, count);
+        return cudaGetLastError();
+    }
+};
 
-cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int vtype,
+cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int layout,
                                 bool dense, cudaStream_t s) {
-    switch (vtype) {
-    case kF32:
-        return dense ? batch_launch_t<float, true>(params, block_begin, count, grid, s)
-                     : batch_launch_t<float, false>(params, block_begin, count, grid, s);
-    case kBF16:
-        return dense ? batch_launch_t<__nv_bfloat16, true>(params, block_begin, count, grid, s)
-                     : batch_launch_t<__nv_bfloat16, false>(params, block_begin, count, grid, s);
-    case kF16:
-        return dense ? batch_launch_t<__half, true>(params, block_begin, count, grid, s)
-                     : batch_launch_t<__half, false>(params, block_begin, count, grid, s);
-    default: return cudaErrorInvalidValue;
+    return with_layout(layout, dense, BatchUpdateLaunch{params, block_begin, count, grid, s}, cudaErrorInvalidValue);
+}
+
+// Resident blocks per SM of the update kernels (from the occupancy calculator).
+struct UpdateOccupancy {
+    bool batch;
+    template <typename T, typename I, bool kDense> int run() const {
+        int nb = 0;
+        const cudaError_t e =
+            batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_update_kernel<T, I, kDense>, kBatchBlock, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, I, kDense>, kUpdateBlock, 0);
+        return e == cudaSuccess && nb > 0 ? nb : 1;
     }
-}
+};
 
-template <typename T, bool kDense>
-static int batch_occ() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_update_kernel<T, kDense>, kBatchBlock, 0) !=
-        cudaSuccess)
-        return 1;
-    return nb > 0 ? nb : 1;
-}
+int batch_update_max_blocks_per_sm(int layout, bool dense) { return with_layout(layout, dense, UpdateOccupancy{true}, 1); }
 
-int batch_update_max_blocks_per_sm(int vtype, bool dense) {
-    switch (vtype) {
-    case kF32: return dense ? batch_occ<float, true>() : batch_occ<float, false>();
-    case kBF16: return dense ? batch_occ<__nv_bfloat16, true>() : batch_occ<__nv_bfloat16, false>();
-    case kF16: return dense ? batch_occ<__half, true>() : batch_occ<__half, false>();
-    default: return 1;
-    }
-}
-
-template <typename T, bool kDense>
-static int occ() {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, kDense>, kUpdateBlock, 0) !=
-        cudaSuccess)
-        return 1;
-    return nb > 0 ? nb : 1;
-}
-
-int update_max_blocks_per_sm(int vtype, bool dense) {
-    switch (vtype) {
-    case kF32: return dense ? occ<float, true>() : occ<float, false>();
-    case kBF16: return dense ? occ<__nv_bfloat16, true>() : occ<__nv_bfloat16, false>();
-    case kF16: return dense ? occ<__half, true>() : occ<__half, false>();
-    default: return 1;
-    }
-}
+int update_max_blocks_per_sm(int layout, bool dense) { return with_layout(layout, dense, UpdateOccupancy{false}, 1); }
 
 __global__ void sample_rows_kernel(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
                                    int64_t *rows) {

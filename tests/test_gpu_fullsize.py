@@ -9,7 +9,8 @@ update, so the tests check what it can compute at any size:
   * after asynchronous epochs at the tuned schedule: the float64 objective
     and gradient at the GPU iterate against the oracle's (1e-12 / 1e-11),
     and abar recomputed from the memory against the oracle's sum rounded to
-    float32 (exact);
+    float32 (within one float32 ulp: the float64 column sums add atomics in
+    no fixed order);
   * 1e-6 relative suboptimality against the f* stored in tests/golden (the
     oracle's certified value for the same generated problem).
 """
@@ -99,7 +100,10 @@ def test_tuned_schedule_evaluations_and_target_at_full_size(workload):
         assert f == pytest.approx(R.objective(p, x64), rel=1e-12)
         g_ref = R.gradient(p, x64)
         assert rel(gr, g_ref) <= 1e-11
-        np.testing.assert_array_equal(abar_new, R.abar_from_scratch(p, alpha.astype(np.float64)).astype(np.float32))
+        # the float64 column sums add atomics in no fixed order; at millions of
+        # columns a few of them round to the neighbouring float32
+        np.testing.assert_array_max_ulp(abar_new, R.abar_from_scratch(p, alpha.astype(np.float64)).astype(np.float32),
+                                        maxulp=1)
         # the tuned schedule reaches the target from x = 0
         asaga.asaga_set_state(c.ctx, np.zeros(p.d, np.float32), np.zeros(p.d, np.float32),
                               np.zeros(p.n, np.float32), 0)
