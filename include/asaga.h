@@ -46,7 +46,8 @@ typedef enum {
     ASAGA_ECUDA = 3,          /* a CUDA call failed (no GPU, launch error, ...) */
     ASAGA_ETIMEOUT = 4,       /* the run stopped at options.timeout_s          */
     ASAGA_EDIVERGED = 5,      /* objective or iterate became non-finite        */
-    ASAGA_ENOTCONVERGED = 6   /* max_epochs reached before the target          */
+    ASAGA_ENOTCONVERGED = 6,  /* max_epochs reached before the target          */
+    ASAGA_ECANCELLED = 7      /* asaga_cancel / asaga_batch_cancel stopped it  */
 } asaga_status;
 
 typedef enum { ASAGA_LOSS_LOGISTIC = 0, ASAGA_LOSS_SQUARED = 1 } asaga_loss;
@@ -209,6 +210,15 @@ asaga_status asaga_create(asaga_ctx **out, const asaga_problem *problem,
 asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subopt,
                        double f_star, asaga_result *res);
 
+/* Asks the asaga_run in progress on ctx (called from another host thread)
+ * to stop: the update kernel polls a flag in mapped host memory every 256
+ * updates of each warp, and asaga_run returns ASAGA_ECANCELLED after the
+ * segment, with the state as the finished updates left it and the context
+ * usable.  Thread-safe; a request made while no run is in progress is
+ * dropped when the next asaga_run starts.  The paper has no counterpart.
+ * EINVAL: ctx NULL. */
+asaga_status asaga_cancel(asaga_ctx *ctx);
+
 /* Picks the number of concurrent warps and the step size for asaga_run.
  * The overlap tau of asynchronous updates grows with the number of warps,
  * and the largest stable step shrinks with tau (Theorem 2: a <= a*(tau)).
@@ -366,6 +376,12 @@ asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_proble
  * ENOTCONVERGED otherwise, EDIVERGED if an objective turned non-finite. */
 asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, const double *f_star,
                              asaga_result *results);
+
+/* Asks the asaga_batch_run in progress (from another host thread) to stop
+ * after the current segment; it returns ASAGA_ECANCELLED with every
+ * instance's state as its updates left it.  Thread-safe; dropped when the
+ * next asaga_batch_run starts.  EINVAL: b NULL. */
+asaga_status asaga_batch_cancel(asaga_batch *b);
 
 /* Per-instance step sizes from shared trials: the schedule is reset to the
  * default, and every trial runs all instances at once for trial_epochs

@@ -21,9 +21,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libasaga.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "asaga.h")
 
-OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDIVERGED, ENOTCONVERGED = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EDIVERGED, ENOTCONVERGED, ECANCELLED = range(8)
 STATUS_NAMES = ["ASAGA_OK", "ASAGA_EINVAL", "ASAGA_ENOMEM", "ASAGA_ECUDA", "ASAGA_ETIMEOUT",
-                "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED"]
+                "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED", "ASAGA_ECANCELLED"]
 LOSS = {"logistic": 0, "squared": 1}
 DTYPE = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 SAMPLING = {"uniform": 0, "permutation": 1}
@@ -131,6 +131,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_recompute_abar_noalloc.restype = i32
     L.asaga_sample_rows.argtypes = [ctypes.c_uint64, i64, i32, ctypes.c_uint64, i64, vp]
     L.asaga_sample_rows.restype = i32
+    L.asaga_cancel.argtypes = [vp]
+    L.asaga_cancel.restype = i32
+    L.asaga_batch_cancel.argtypes = [vp]
+    L.asaga_batch_cancel.restype = i32
     L.asaga_destroy.argtypes = [vp]
     L.asaga_destroy.restype = None
     L.asaga_batch_create.argtypes = [P(vp), i32, P(asaga_problem), P(asaga_options)]
@@ -243,6 +247,11 @@ def asaga_autotune(ctx: int, trial_epochs: float = 0.0) -> dict:
     r = asaga_tune_result()
     _check(ctx, load().asaga_autotune(ctx, float(trial_epochs), ctypes.byref(r)))
     return r.as_dict()
+
+
+def asaga_cancel(ctx: int) -> None:
+    """Asks the asaga_run in progress on ctx (in another thread) to stop."""
+    _check(ctx, load().asaga_cancel(ctx))
 
 
 def asaga_measure_overlap(ctx: int, epochs: float = 1.0) -> dict:
@@ -388,6 +397,11 @@ def asaga_batch_run(b: int, count: int, max_epochs: float, target: float = 0.0, 
     if s in (EINVAL, ENOMEM, ECUDA):
         raise AsagaError(s, load().asaga_batch_last_error(b).decode())
     return s, list(res)
+
+
+def asaga_batch_cancel(b: int) -> None:
+    """Asks the asaga_batch_run in progress (in another thread) to stop."""
+    _bcheck(b, load().asaga_batch_cancel(b))
 
 
 def asaga_batch_autotune(b: int, count: int, trial_epochs: float = 0.0) -> list:

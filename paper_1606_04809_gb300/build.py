@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in results:
             print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-lpthread"], capture_output=True, text=True)
+    r = subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-lpthread", "-ldl"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

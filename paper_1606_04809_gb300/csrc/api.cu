@@ -13,6 +13,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "asaga.h"
 #include "asaga_internal.h"
 
@@ -68,6 +70,8 @@ struct asaga_ctx {
     int64_t idx_cap = 0;
     double *hout = nullptr;  // pinned mirror of dout
     int *hstatus = nullptr;  // pinned
+    int *h_cancel = nullptr;  // mapped pinned flag set by asaga_cancel
+    int *d_cancel = nullptr;  // its device address
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 
     std::string err;
@@ -81,6 +85,7 @@ struct asaga_batch {
     bool own_stream = false;
     int device = 0;
     int layout = kF32;  // the instances' common layout (ValType | kIdx16)
+    int cancel = 0;     // set by asaga_batch_cancel (atomic)
     bool dense = false;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -103,8 +108,16 @@ namespace {
 
 thread_local std::string g_create_err;
 
-const char *kStatusNames[] = {"ASAGA_OK", "ASAGA_EINVAL", "ASAGA_ENOMEM", "ASAGA_ECUDA",
-                              "ASAGA_ETIMEOUT", "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED"};
+const char *kStatusNames[] = {"ASAGA_OK",        "ASAGA_EINVAL",    "ASAGA_ENOMEM",        "ASAGA_ECUDA",
+                              "ASAGA_ETIMEOUT",  "ASAGA_EDIVERGED", "ASAGA_ENOTCONVERGED", "ASAGA_ECANCELLED"};
+
+// NVTX range for profilers (a no-op unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 asaga_status fail(std::string *err, asaga_status s, const std::string &msg) {
     if (err) *err = msg;
@@ -431,6 +444,7 @@ asaga_status apply_compact(asaga_ctx *c, bool rows_equal, bool idx16, std::strin
 }
 
 asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
+    NvtxRange range("asaga_create");
     int64_t mrl = 0;
     TRY(validate(p, o, &mrl, err));
     CK(cudaGetDevice(&c->device), "cudaGetDevice");
@@ -516,6 +530,9 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     TRY(dev_alloc(&c->status, 4, c, err, "alloc status"));
     CK(cudaMallocHost((void **)&c->hout, 8 * sizeof(double)), "alloc pinned");
     CK(cudaMallocHost((void **)&c->hstatus, 4 * sizeof(int)), "alloc pinned");
+    CK(cudaHostAlloc((void **)&c->h_cancel, sizeof(int), cudaHostAllocMapped), "alloc cancel flag");
+    *c->h_cancel = 0;
+    CK(cudaHostGetDevicePointer((void **)&c->d_cancel, c->h_cancel, 0), "cancel flag address");
 
     // D from the column counts (Sec. 2); dense rows give D = 1
     int *count = nullptr;
@@ -593,6 +610,7 @@ void release(asaga_ctx *c) {
     cudaFree(c->hot_col);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstatus) cudaFreeHost(c->hstatus);
+    if (c->h_cancel) cudaFreeHost(c->h_cancel);
     for (auto &ev : c->ev)
         if (ev) cudaEventDestroy(ev);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -627,6 +645,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.deadline_ns = 0;
     u.status = c->status;
     u.trace = nullptr;
+    u.cancel = nullptr;  // only asaga_run honours asaga_cancel
     return u;
 }
 
@@ -664,15 +683,23 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
     r.rel_subopt = NAN;
     const int64_t launches0 = c->launches;
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "memset status");
+    __atomic_store_n(c->h_cancel, 0, __ATOMIC_SEQ_CST);
     double epochs_done = 0;
     asaga_status st = target > 0 ? ASAGA_ENOTCONVERGED : ASAGA_OK;
     int64_t seg = 0;
     while (epochs_done < max_epochs) {
+        NvtxRange range("asaga_run segment");
+        if (__atomic_load_n(c->h_cancel, __ATOMIC_SEQ_CST)) {  // requested between segments
+            st = ASAGA_ECANCELLED;
+            fail(err, st, "cancelled");
+            break;
+        }
         const double ep = std::min((double)c->epochs_per_segment, max_epochs - epochs_done);
         const int64_t count = (int64_t)std::llround(ep * (double)c->n);
         UpdateParams u = update_params(c);
         u.t_begin = (uint64_t)c->updates_done;
         u.count = count;
+        u.cancel = c->d_cancel;
         if (c->timeout_s > 0) {
             const double left = c->timeout_s -
                                 std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -708,6 +735,11 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
         if (*c->hstatus & 1) {
             st = ASAGA_ETIMEOUT;
             fail(err, st, "timeout");
+            break;
+        }
+        if (*c->hstatus & 8) {
+            st = ASAGA_ECANCELLED;
+            fail(err, st, "cancelled");
             break;
         }
         if (!std::isfinite(r.f_last)) {
@@ -895,6 +927,7 @@ asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, int E, dou
 }
 
 asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
+    NvtxRange range("asaga_autotune");
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
@@ -1357,7 +1390,14 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
     int64_t seg = 0;
     int n_active = b->count;
     const int64_t launches0 = b->launches;
+    __atomic_store_n(&b->cancel, 0, __ATOMIC_SEQ_CST);
+    bool cancelled = false;
     while (epochs < max_epochs && n_active > 0) {
+        if (__atomic_load_n(&b->cancel, __ATOMIC_SEQ_CST)) {
+            cancelled = true;
+            break;
+        }
+        NvtxRange range("asaga_batch_run segment");
         const double ep = std::min((double)b->epochs_per_segment, max_epochs - epochs);
         for (int i = 0; i < b->count; ++i) {
             asaga_ctx *c = b->ctx[i];
@@ -1402,16 +1442,19 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
         if (!std::isfinite(r[i].f_last)) st = ASAGA_EDIVERGED;
         else if (target > 0 && !(r[i].rel_subopt <= target) && st == ASAGA_OK) st = ASAGA_ENOTCONVERGED;
     }
+    if (cancelled) st = ASAGA_ECANCELLED;
     if (results) std::copy(r.begin(), r.end(), results);
-    if (st != ASAGA_OK) fail(err, st, st == ASAGA_EDIVERGED ? "an instance diverged" : "max_epochs reached before the target");
+    if (st != ASAGA_OK)
+        fail(err, st, st == ASAGA_EDIVERGED ? "an instance diverged"
+                      : st == ASAGA_ECANCELLED ? "cancelled" : "max_epochs reached before the target");
     return st;
 }
 
 // Per-instance step sizes from shared trials: every trial runs all
-// instances at once with gamma_i = s * gamma0_i for one scale s of the
-// ladder 2^(-k/2); each instance keeps the scale under which its float64
-// |grad f_i|^2 fell fastest (monotonically over the trial's last two epochs),
-// one notch lower as a margin.
+// instances at once with gamma_i = s * gamma0_i for one scale s of the ladder
+// 2^(-k/2) and records each instance's float64 |grad f_i|^2 after every
+// epoch; each instance then takes, one notch inside its largest converging
+// step, the step with the fewest predicted epochs (the single-problem tests).
 asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
     CK(cudaSetDevice(b->device), "cudaSetDevice");
     const int E = trial_epochs > 0 ? std::max(5, (int)std::ceil(trial_epochs)) : 16;
@@ -1567,6 +1610,18 @@ asaga_status asaga_run(asaga_ctx *c, double max_epochs, double target, double f_
     return run_impl(c, max_epochs, target, f_star, res, &c->err);
 }
 
+asaga_status asaga_cancel(asaga_ctx *c) {
+    if (!c) return ASAGA_EINVAL;
+    __atomic_store_n(c->h_cancel, 1, __ATOMIC_SEQ_CST);
+    return ASAGA_OK;
+}
+
+asaga_status asaga_batch_cancel(asaga_batch *b) {
+    if (!b) return ASAGA_EINVAL;
+    __atomic_store_n(&b->cancel, 1, __ATOMIC_SEQ_CST);
+    return ASAGA_OK;
+}
+
 asaga_status asaga_autotune(asaga_ctx *c, double trial_epochs, asaga_tune_result *res) {
     if (!c) return ASAGA_EINVAL;
     return autotune_impl(c, trial_epochs, res, &c->err);
@@ -1694,7 +1749,7 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
 const char *asaga_last_error(const asaga_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 const char *asaga_status_string(asaga_status s) {
-    if ((int)s < 0 || (int)s > 6) return "ASAGA_UNKNOWN";
+    if ((int)s < 0 || (int)s > 7) return "ASAGA_UNKNOWN";
     return kStatusNames[(int)s];
 }
 

@@ -47,7 +47,8 @@ struct UpdateParams {
     int fence_each;           // 1: fence after every update (single-warp order)
     int plain_writes;         // 1: non-atomic load-add-store instead of reductions (diagnostic)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
-    int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range
+    const volatile int *cancel;  // nonzero: stop (a flag in mapped host memory), or nullptr
+    int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range, bit 3: cancelled
     uint64_t *trace;          // 2 * count: %globaltimer before the reads / after the writes of update t (or nullptr)
 };
 

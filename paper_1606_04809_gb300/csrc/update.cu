@@ -315,10 +315,19 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
             __threadfence();
             __syncwarp();
         }
-        if (deadline && ((++done & 31) == 0)) {
-            const uint64_t now = __shfl_sync(kFull, globaltimer_ns(), 0);
-            if (now > deadline) {
-                if (lane == 0) atomicOr(P.status, 1);
+        if ((deadline || P.cancel) && ((++done & 31) == 0)) {
+            // the deadline every 32 updates; the host's cancel flag (a read of
+            // mapped host memory) every 256
+            int stop = 0;
+            if (lane == 0) {
+                if (deadline && globaltimer_ns() > deadline)
+                    stop = 1;
+                else if (P.cancel && (done & 255) == 0 && *P.cancel)
+                    stop = 8;
+            }
+            stop = __shfl_sync(kFull, stop, 0);
+            if (stop) {
+                if (lane == 0) atomicOr(P.status, stop);
                 break;
             }
         }

@@ -148,3 +148,10 @@ def test_sampler_arguments_are_checked_before_any_cuda_call(lib):
     assert L.asaga_sample_rows(1, 10, 0, 0, 4, None) == asaga.EINVAL
     assert L.asaga_sample_rows(1, (1 << 62) + 1, 1, 0, 4, p) == asaga.EINVAL
     assert L.asaga_sample_rows(1, 10, 0, 0, 0, None) == asaga.OK  # nothing to do
+
+
+def test_cancel_needs_a_context(lib):
+    L = asaga.load()
+    assert L.asaga_cancel(None) == asaga.EINVAL
+    assert L.asaga_batch_cancel(None) == asaga.EINVAL
+    assert asaga.asaga_status_string(asaga.ECANCELLED) == "ASAGA_ECANCELLED"

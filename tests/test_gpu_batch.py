@@ -77,3 +77,21 @@ def test_batch_schedule_and_errors():
     mixed = [ps[0], synth.dense_ridge(500, 10, storage="f32", seed=64)]
     with pytest.raises(asaga.AsagaError):
         asaga.Batch(mixed, storage="f32")
+
+
+def test_batch_cancel_from_another_thread():
+    import threading
+    ps = small_batch("f32", count=3, seed=63)
+    with asaga.Batch(ps, storage="f32", epochs_per_segment=1) as b:
+        out = {}
+        th = threading.Thread(target=lambda: out.setdefault("res", asaga.asaga_batch_run(b.b, b.count, 1e6)))
+        th.start()
+        import time
+        time.sleep(0.3)
+        asaga.asaga_batch_cancel(b.b)
+        th.join(timeout=60)
+        assert not th.is_alive()
+        s, res = out["res"]
+        assert s == asaga.ECANCELLED and all(0 < r.epochs < 1e6 for r in res)
+        s2, res2 = asaga.asaga_batch_run(b.b, b.count, 2)
+        assert s2 == asaga.OK and all(np.isfinite(r.f_last) for r in res2)

@@ -293,6 +293,32 @@ def test_timeout_returns_status_and_keeps_context_usable():
         assert np.isfinite(f)
 
 
+def test_cancel_from_another_thread_stops_a_run_and_keeps_the_context_usable():
+    import threading
+    import time
+    p = synth.rcv1_like(seed=22, n=60000, d=6000)
+    with asaga.Context(p, seed=5, max_warps=256, gamma=0.05) as c:
+        out = {}
+
+        def run():
+            t0 = time.perf_counter()
+            out["res"] = asaga.asaga_run(c.ctx, 1e6)
+            out["t"] = time.perf_counter() - t0
+
+        th = threading.Thread(target=run)
+        th.start()
+        time.sleep(0.3)
+        asaga.asaga_cancel(c.ctx)
+        th.join(timeout=60)
+        assert not th.is_alive()
+        s, r = out["res"]
+        assert s == asaga.ECANCELLED and 0 < r.epochs < 1e6 and out["t"] < 10
+        # a new run starts clean and the state is finite
+        s2, r2 = asaga.asaga_run(c.ctx, 2)
+        assert s2 == asaga.OK and np.isfinite(r2.f_last)
+        assert np.all(np.isfinite(asaga.asaga_get_state(c.ctx)[0]))
+
+
 def test_state_roundtrip_and_resume():
     p = synth.small_logistic()
     with asaga.Context(p, seed=8) as c:
