@@ -165,9 +165,10 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(workload):
-    """Per-launch DRAM bytes of the update kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+def ncu_summary(workload):
+    """Per-launch DRAM bytes and the L2 throughput (% of peak) of the update
+    kernel from the committed ncu summary, if it was taken on the current
+    kernel source; None otherwise."""
     path = os.path.join(ROOT, "profiles", f"update_kernel_{workload}.md")
     src = os.path.join(ROOT, "paper_1606_04809_gb300", "csrc", "update.cu")
     if not os.path.exists(path):
@@ -181,9 +182,15 @@ def ncu_traffic(workload):
     if kv.get("update.cu sha256") != sha:
         return None
     try:
-        return int(float(kv["traffic_bytes_per_launch"]))
+        out = {"traffic": int(float(kv["traffic_bytes_per_launch"]))}
     except Exception:
         return None
+    for key, name in (("l2_throughput_pct_of_peak", "l2_pct"), ("dram_throughput_pct_of_peak", "dram_pct")):
+        try:
+            out[name] = float(kv[key])
+        except Exception:
+            pass
+    return out
 
 
 def update_hbm_bytes(p, storage, info=None):
@@ -531,9 +538,12 @@ def main():
     hbm_bytes = update_hbm_bytes(p, storage, info)
     peak, peak_kind = measured_peak_hbm()
     achieved = hbm_bytes / (upd_ms * 1e-3) / 1e9
+    ncu = ncu_summary(args.workload) or {}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(args.workload), "kernel": "update_kernel (one launch = one epoch)",
-                "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": upd_ms, "peak_source": peak_kind}
+                "traffic": ncu.get("traffic"), "kernel": "update_kernel (one launch = one epoch)",
+                "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": upd_ms, "peak_source": peak_kind,
+                "l2_throughput_pct_of_peak_ncu": ncu.get("l2_pct"),
+                "dram_throughput_pct_of_peak_ncu": ncu.get("dram_pct")}
 
     # time to 1e-6 from x = 0
     ttt = None

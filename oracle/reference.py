@@ -13,7 +13,7 @@ for a reader to check by eye against the paper:
 * ``dense_saga_step`` -- the original SAGA update (Eq. SAGAupdate), used only
   to check the sparse variant against it;
 * ``lagged_saga`` -- the same dense SAGA iteration with lagged updates
-  (App. C), the serial baseline the paper compares Sparse SAGA with;
+  (App. F), the serial baseline the paper compares Sparse SAGA with;
 * ``splitmix64`` / ``sampler_indices`` -- the published SplitMix64 generator
   and the row sampling built on it, written independently of the solver's;
 * ``newton`` / ``ridge_closed_form`` -- exact minimisers used to certify f*.
@@ -203,7 +203,7 @@ def sparse_saga(p, state: State, idx: np.ndarray, gamma: float, D: Optional[np.n
 
 def lagged_saga(p, state: State, idx: np.ndarray, gamma: float) -> State:
     """Runs len(idx) steps of dense SAGA (Eq. SAGAupdate) in place with the
-    lagged-update scheme of App. C (C file ``saga_ref.c``): per step only the
+    lagged-update scheme of App. F (C file ``saga_ref.c``): per step only the
     sampled support is touched, the other coordinates catch up in closed
     form when next read, and all of them at the end.  For comparison with
     Sparse SAGA only; the solver has no counterpart."""

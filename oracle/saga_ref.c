@@ -103,7 +103,7 @@ void oracle_row_derivatives(int64_t n, const int64_t *row_ptr, const int32_t *co
 }
 
 /*
- * Serial SAGA with lagged updates (App. C.1 and C.2, the "just-in-time"
+ * Serial SAGA with lagged updates (App. F.1 and F.2, the "just-in-time"
  * scheme of the SAG/SAGA literature that the paper compares Sparse SAGA with).
  * It computes the dense SAGA iteration (Eq. SAGAupdate with the l2 term's
  * gradient lambda x taken exactly):

@@ -345,7 +345,7 @@ def test_serial_sparse_saga_is_stable_with_heavy_reweighting():
     assert abs(res["fstar"] - R.objective(p, xs)) <= 1e-11 * abs(R.objective(p, xs))
 
 
-# ------------------------------------------------------------ lagged updates (App. C)
+# ------------------------------------------------------------ lagged updates (App. F)
 
 @pytest.mark.parametrize("lam", [0.05, 0.0])
 def test_lagged_saga_equals_dense_saga(lam):
@@ -378,7 +378,7 @@ def test_lagged_pin_catches_a_missing_catch_up():
 
 
 def test_lagged_and_sparse_saga_converge_alike():
-    """App. C.1: on sparse data Sparse SAGA and lagged-update SAGA need about
+    """App. F.1: on sparse data Sparse SAGA and lagged-update SAGA need about
     the same number of passes over the data."""
     p = synth.sparse_logistic(3000, 600, k_mean=8, k_min=2, k_max=30, zipf_s=1.1, values="abs_normal",
                               storage="f64", seed=5, name="appC")
@@ -471,3 +471,23 @@ def test_cpu_asaga_with_threads_reaches_the_optimum():
         run.run(st, p.n, gamma, seed=3)
     assert (R.objective(p, st.x) - fs) / abs(fs) < 1e-8
     assert np.max(np.abs(st.abar - R.abar_from_scratch(p, st.alpha))) < 1e-10
+
+
+# ------------------------------------------------------------ mixed precision: drift of the optimum
+
+@pytest.mark.parametrize("values,storage", [("binary", "bf16"), ("abs_normal", "bf16"), ("abs_normal", "f16")])
+def test_quantisation_moves_the_optimum_by_a_reported_amount(values, storage):
+    """The solver's f* is the optimum of the stored (quantised) matrix; the
+    float64 matrix's optimum differs.  This reports the relative gap (it is
+    not a tolerance of the solver: the 1e-6 target is measured against the
+    quantised problem's own f*) and bounds it loosely."""
+    p = synth.sparse_logistic(3000, 800, k_mean=20, k_min=2, k_max=60, zipf_s=1.1, storage="f64", seed=9,
+                              values=values)
+    q = synth.Problem(**{**p.__dict__})
+    q.values = synth.to_storage_grid(p.values, storage)
+    q.storage = storage
+    f64 = R.objective(p, R.newton(p))
+    fq = R.objective(q, R.newton(q))
+    drift = abs(fq - f64) / abs(f64)
+    print(f"{values} {storage}: f*(float64 A) = {f64:.12f}, f*(stored A) = {fq:.12f}, relative gap {drift:.2e}")
+    assert 0 < drift < 1e-3
