@@ -358,7 +358,8 @@ typedef struct asaga_batch asaga_batch;
  * gamma, seed per instance).  All instances share options[0].storage_dtype,
  * the sparse or dense layout, options[0].epochs_per_segment and
  * options[0].abar_recompute_every, and run on options[0].cuda_stream.  The
- * initial schedule gives instance i warps in proportion to its nonzeros (a
+ * initial schedule gives instance i warps in proportion to n_i (1 + k_i/128),
+ * k_i its mean row length (an update's cost is mostly a fixed latency; a
  * multiple of 4, at least 4, at most max(4, n_i/32), which keeps tau near
  * n_i/10 as Theorem 2 asks) within the warps that
  * can be resident at once.  EINVAL as asaga_create, or for mixed dtypes or

@@ -1236,14 +1236,22 @@ asaga_status batch_layout(asaga_batch *b, std::string *err) {
 // nonzeros, multiples of 4, at least 4, at most max(4, n_i/16) (which keeps
 // each instance's overlap far below n_i/10), within the resident maximum.
 asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
+    // an update costs a fixed latency (sample, row_ptr, gathers, reduction)
+    // plus a little per entry: weight instance i by n_i (1 + k_i/128), k_i
+    // its mean row length, so that every instance's epoch takes about as
+    // long and no instance holds the shared segments back
     const int64_t budget = (int64_t)b->resident_blocks * 4;
+    auto weight = [](const asaga_ctx *c) {
+        const double k = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+        return (double)c->n * (1.0 + k / 128.0);
+    };
     double total = 0;
-    for (auto *c : b->ctx) total += (double)std::max<int64_t>(c->nnz, c->n);
+    for (auto *c : b->ctx) total += weight(c);
     b->warps.assign(b->count, 4);
     int64_t used = 0;
     for (int i = 0; i < b->count; ++i) {
         const asaga_ctx *c = b->ctx[i];
-        const double share = (double)std::max<int64_t>(c->nnz, c->n) / total * (double)budget;
+        const double share = weight(c) / total * (double)budget;
         int64_t w = std::max<int64_t>(4, ((int64_t)share / 4) * 4);
         w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 32 / 4) * 4));  // tau below ~n/10 (Theorem 2)
         b->warps[i] = (int)w;
