@@ -583,6 +583,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
             c = asaga.asaga_create(prob, o)
+            asaga.asaga_set_schedule(c, info["warps"], info["gamma"], info["warps_per_block"])
             asaga.asaga_run(c, 1)
             asaga.load().asaga_get_state(c, xh.data_ptr(), None, None)
             asaga.asaga_destroy(c)

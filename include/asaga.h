@@ -205,7 +205,10 @@ asaga_status asaga_create(asaga_ctx **out, const asaga_problem *problem,
  * (f - f_star) / |f_star| <= target_rel_subopt (returns OK), or after
  * max_epochs (returns OK if target_rel_subopt <= 0, else ENOTCONVERGED).
  * Continues from the current state; the sampler stream continues too.
- * EDIVERGED if f turns non-finite; ETIMEOUT at options.timeout_s.
+ * EDIVERGED if f turns non-finite; ETIMEOUT at options.timeout_s;
+ * ECANCELLED after asaga_cancel; ECUDA if the kernel found a malformed row
+ * range on the device.  After ETIMEOUT or ECANCELLED, res->updates and the
+ * sampler position count the stopped segment as if it had completed.
  * res may be NULL. */
 asaga_status asaga_run(asaga_ctx *ctx, double max_epochs, double target_rel_subopt,
                        double f_star, asaga_result *res);
@@ -226,7 +229,8 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  * the iterate stalls on a plateau (logistic loss) or diverges (squared loss);
  * below it the epochs needed depend on the step only, while the epoch time
  * falls with the number of warps.  Steps are gamma0 * 2^(-k/2), gamma0 =
- * options.gamma or 1/(3L), k = -4..16.  Each trial starts from x = 0,
+ * options.gamma or 1/(3L), k = -3..16 (the largest, 0.94/L, below 1/L).
+ * Each trial starts from x = 0,
  * alpha = 0 and records the float64 |grad f|^2 after every epoch:
  *  1. frontier: at min(1024, n/32, resident) warps (Theorem 2 asks for
  *     tau < n/10, and tau measures 1.5 to 4 times the warps; no candidate
@@ -335,6 +339,14 @@ asaga_status asaga_set_state(asaga_ctx *ctx, const float *x, const float *abar,
 
 asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
 
+/* Sets the schedule asaga_run uses, e.g. one asaga_autotune found for the
+ * same problem earlier (asaga_get_info reports warps, gamma and
+ * warps_per_block): warps >= 1 (at most the resident maximum), gamma > 0,
+ * warps_per_block 0 (eight warps per block) or the value asaga_get_info
+ * reported (spread over the SMs when below 8).  EINVAL on other values or
+ * in deterministic mode (one warp). */
+asaga_status asaga_set_schedule(asaga_ctx *ctx, int warps, double gamma, int warps_per_block);
+
 /* Reason for the last failure of a call on ctx (or, when ctx is NULL, of
  * the calling thread's last asaga_create, asaga_sample_rows or
  * asaga_recompute_abar_noalloc); never NULL. */
@@ -374,7 +386,8 @@ asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_proble
  * device time of the shared segments up to the one after which it stopped,
  * i.e. its time to target inside the batch.  f_star may be NULL when
  * target <= 0.  OK when every instance reached the target (or target <= 0),
- * ENOTCONVERGED otherwise, EDIVERGED if an objective turned non-finite. */
+ * ENOTCONVERGED otherwise, EDIVERGED if an objective turned non-finite,
+ * ECANCELLED after asaga_batch_cancel. */
 asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, const double *f_star,
                              asaga_result *results);
 
@@ -384,15 +397,21 @@ asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, c
  * next asaga_batch_run starts.  EINVAL: b NULL. */
 asaga_status asaga_batch_cancel(asaga_batch *b);
 
-/* Per-instance step sizes from shared trials: the schedule is reset to the
- * default, and every trial runs all instances at once for trial_epochs
- * epochs (<= 0: 16) from x = 0 with gamma_i = s * gamma0_i, s = 2^(-k/2) on
- * the ladder k = -4..12 (stopping once smaller steps help no instance),
- * recording each float64 |grad f_i|^2 after every epoch.  Each instance
- * takes the largest step that converges (the test of asaga_autotune), and
- * then, from one notch inside it on, the step with the fewest predicted
- * epochs (the trend test of asaga_autotune).  Leaves every instance at
- * x = 0.  results[i] may be NULL; its score is 1 / predicted epochs. */
+/* Per-instance step sizes, and warps, from shared trials.  Every trial runs
+ * all instances at once for trial_epochs epochs (<= 0: 16) from x = 0 with
+ * gamma_i = s * gamma0_i, s = 2^(-k/2) on the ladder k = -3..12 (stopping
+ * once smaller steps help no instance), recording each float64
+ * |grad f_i|^2 after every epoch.  Each instance takes the largest step
+ * that converges (the test of asaga_autotune) and then, from one notch
+ * inside it on, the step with the fewest predicted epochs (the trend test
+ * of asaga_autotune); an instance whose prediction lies beyond twice the
+ * trial runs on alone (up to 8x longer) to refine it.  Two passes: under
+ * the default schedule, then with
+ * warps in proportion to each instance's predicted work (epochs x epoch
+ * cost, within the same caps); the second is kept unless an instance
+ * predicted under the first has no prediction under it.  Leaves
+ * every instance at x = 0.  results[i] may be NULL; its score is
+ * 1 / predicted epochs. */
 asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);
 
 /* Overrides the schedule: warps[i] (rounded up to a multiple of 4) and/or

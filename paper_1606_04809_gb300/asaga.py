@@ -133,6 +133,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_sample_rows.restype = i32
     L.asaga_cancel.argtypes = [vp]
     L.asaga_cancel.restype = i32
+    L.asaga_set_schedule.argtypes = [vp, i32, dbl, i32]
+    L.asaga_set_schedule.restype = i32
     L.asaga_batch_cancel.argtypes = [vp]
     L.asaga_batch_cancel.restype = i32
     L.asaga_destroy.argtypes = [vp]
@@ -247,6 +249,10 @@ def asaga_autotune(ctx: int, trial_epochs: float = 0.0) -> dict:
     r = asaga_tune_result()
     _check(ctx, load().asaga_autotune(ctx, float(trial_epochs), ctypes.byref(r)))
     return r.as_dict()
+
+
+def asaga_set_schedule(ctx: int, warps: int, gamma: float, warps_per_block: int = 0) -> None:
+    _check(ctx, load().asaga_set_schedule(ctx, int(warps), float(gamma), int(warps_per_block)))
 
 
 def asaga_cancel(ctx: int) -> None:

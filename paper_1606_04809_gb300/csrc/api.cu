@@ -95,7 +95,8 @@ struct asaga_batch {
     int grid = 0;
     int eval_grid = 1;             // blocks per instance in the batched objective
     UpdateParams *d_up = nullptr, *h_up = nullptr;
-    EvalParams *d_ev = nullptr;
+    EvalParams *d_ev = nullptr, *h_ev = nullptr;  // h_ev pinned, uploaded every segment
+    std::vector<EvalParams> ev_full;              // every instance's evaluation parameters
     int *d_block_begin = nullptr;
     double *d_partial = nullptr, *d_f = nullptr, *h_f = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -933,7 +934,10 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const int E_race = trial_epochs > 0 ? std::max(4, (int)std::ceil(trial_epochs)) : 24;
     const int E_probe = std::min(16, E_race);
-    constexpr int kTop = -4, kBottom = 16;  // steps gamma0 * 2^(-k/2), k in [kTop, kBottom]
+    // steps gamma0 * 2^(-k/2), k in [kTop, kBottom]; the largest, 2^1.5 gamma0 =
+    // 0.94/L (gamma0 = 1/(3L)), stays below 1/L, past which a serial run
+    // of SAGA is not expected to be stable either
+    constexpr int kTop = -3, kBottom = 16;
     auto step = [&](int k) { return c->gamma_base * std::pow(2.0, -0.5 * k); };
     // Theorem 2 wants the overlap tau below n/10; measured, tau is 1.5 to 4
     // times the number of warps: at most n/32 warps
@@ -1206,6 +1210,7 @@ void batch_release(asaga_batch *b) {
     cudaFree(b->d_f);
     if (b->h_up) cudaFreeHost(b->h_up);
     if (b->h_f) cudaFreeHost(b->h_f);
+    if (b->h_ev) cudaFreeHost(b->h_ev);
     for (auto &e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1232,28 +1237,28 @@ asaga_status batch_layout(asaga_batch *b, std::string *err) {
     return ASAGA_OK;
 }
 
-// Default schedule: warps spread over the instances in proportion to their
-// nonzeros, multiples of 4, at least 4, at most max(4, n_i/16) (which keeps
-// each instance's overlap far below n_i/10), within the resident maximum.
-asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
-    // an update costs a fixed latency (sample, row_ptr, gathers, reduction)
-    // plus a little per entry: weight instance i by n_i (1 + k_i/128), k_i
-    // its mean row length, so that every instance's epoch takes about as
-    // long and no instance holds the shared segments back
+// Cost of one epoch of instance i relative to the others: an update costs a
+// fixed latency (sample, row_ptr, gathers, reduction) plus a little per
+// entry, so n_i (1 + k_i/128), k_i its mean row length.
+double batch_epoch_cost(const asaga_ctx *c) {
+    const double k = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+    return (double)c->n * (1.0 + k / 128.0);
+}
+
+// Warps in proportion to weight[i] (a multiple of 4, at least 4, at most
+// max(4, n_i/32) so that tau stays near n_i/10 as Theorem 2 asks), within
+// the warps that can be resident at once.
+asaga_status batch_weighted_schedule(asaga_batch *b, const std::vector<double> &weight, std::string *err) {
     const int64_t budget = (int64_t)b->resident_blocks * 4;
-    auto weight = [](const asaga_ctx *c) {
-        const double k = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
-        return (double)c->n * (1.0 + k / 128.0);
-    };
     double total = 0;
-    for (auto *c : b->ctx) total += weight(c);
+    for (double w : weight) total += w;
     b->warps.assign(b->count, 4);
     int64_t used = 0;
     for (int i = 0; i < b->count; ++i) {
         const asaga_ctx *c = b->ctx[i];
-        const double share = weight(c) / total * (double)budget;
+        const double share = total > 0 ? weight[i] / total * (double)budget : 4.0;
         int64_t w = std::max<int64_t>(4, ((int64_t)share / 4) * 4);
-        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 32 / 4) * 4));  // tau below ~n/10 (Theorem 2)
+        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 32 / 4) * 4));
         b->warps[i] = (int)w;
         used += w;
     }
@@ -1264,6 +1269,14 @@ asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
         used -= 4;
     }
     return batch_layout(b, err);
+}
+
+// Default schedule: every instance's epoch takes about as long, so that no
+// instance holds the shared segments back.
+asaga_status batch_default_schedule(asaga_batch *b, std::string *err) {
+    std::vector<double> w(b->count);
+    for (int i = 0; i < b->count; ++i) w[i] = batch_epoch_cost(b->ctx[i]);
+    return batch_weighted_schedule(b, w, err);
 }
 
 asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *problems,
@@ -1321,6 +1334,7 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
     b->eval_grid = std::max(1, std::min(64, (prop.multiProcessorCount * 8 + count - 1) / count));
     CK(cudaMallocHost((void **)&b->h_up, count * sizeof(UpdateParams)), "alloc pinned");
     CK(cudaMallocHost((void **)&b->h_f, count * sizeof(double)), "alloc pinned");
+    CK(cudaMallocHost((void **)&b->h_ev, count * sizeof(EvalParams)), "alloc pinned");
     TRY(dev_alloc(&b->d_up, count, b->ctx[0], err, "alloc params"));
     TRY(dev_alloc(&b->d_ev, count, b->ctx[0], err, "alloc params"));
     TRY(dev_alloc(&b->d_block_begin, count, b->ctx[0], err, "alloc schedule"));
@@ -1332,7 +1346,9 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
         b->h_up[i].count = 0;
         b->h_up[i].fence_each = 0;
         ev[i] = eval_params(b->ctx[i]);
+        b->h_ev[i] = ev[i];
     }
+    b->ev_full = ev;
     CK(cudaMemcpyAsync(b->d_ev, ev.data(), count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
        "copy params");
     TRY(batch_default_schedule(b, err));
@@ -1346,6 +1362,8 @@ asaga_status batch_enqueue_segment(asaga_batch *b, std::string *err) {
        "copy params");
     CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->layout, b->dense, b->stream),
        "batch update kernel");
+    CK(cudaMemcpyAsync(b->d_ev, b->h_ev, b->count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
+       "copy eval params");
     CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->layout, b->dense, b->d_partial, b->d_f, b->stream),
        "batch objective");
     CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
@@ -1413,6 +1431,9 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
             u.gamma = (float)c->gamma;
             u.t_begin = (uint64_t)c->updates_done;
             u.count = active[i] ? (int64_t)std::llround(ep * (double)c->n) : 0;
+            // a finished instance also leaves the segment's objective (no rows, no columns)
+            b->h_ev[i] = b->ev_full[i];
+            if (!active[i]) b->h_ev[i].n = b->h_ev[i].d = 0;
         }
         float ms = 0;
         TRY(batch_segment(b, &ms, err));
@@ -1442,6 +1463,10 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
             TRY(stream_sync(b->ctx[0], err));
         }
     }
+    for (int i = 0; i < b->count; ++i) b->h_ev[i] = b->ev_full[i];  // later segments evaluate every instance
+    CK(cudaMemcpyAsync(b->d_ev, b->h_ev, b->count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
+       "copy eval params");
+    TRY(stream_sync(b->ctx[0], err));
     const double wall = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     asaga_status st = ASAGA_OK;
     for (int i = 0; i < b->count; ++i) {
@@ -1463,12 +1488,15 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
 // 2^(-k/2) and records each instance's float64 |grad f_i|^2 after every
 // epoch; each instance then takes, one notch inside its largest converging
 // step, the step with the fewest predicted epochs (the single-problem tests).
-asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
-    CK(cudaSetDevice(b->device), "cudaSetDevice");
-    const int E = trial_epochs > 0 ? std::max(5, (int)std::ceil(trial_epochs)) : 16;
-    constexpr int kTop = -4, kBottom = 12;
+// One pass of shared trials under the current schedule: every trial runs
+// all instances at once for E epochs with gamma_i = 2^(-k/2) gamma0_i (k on
+// the ladder, shared), recording each instance's float64 |grad f_i|^2 after
+// every epoch.  Per instance: kc = one notch inside the largest converging
+// step, or a smaller step with fewer predicted epochs; pc = those epochs.
+asaga_status batch_tune_pass(asaga_batch *b, int E, std::vector<int> *kc_out, std::vector<double> *pc_out,
+                             int *trials, double *seconds, std::string *err) {
+    constexpr int kTop = -3, kBottom = 12;  // the single-problem ladder's top, 0.94/L
     const int nk = kBottom - kTop + 1;
-    TRY(batch_default_schedule(b, err));
     const int N = b->count;
     std::vector<double> g0(N), g(N);
     auto grads = [&](std::vector<double> &out) -> asaga_status {
@@ -1483,12 +1511,9 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
     };
     for (auto *c : b->ctx) TRY(reset_state(c, err));
     TRY(grads(g0));
-    // per instance and ladder position: converging?  predicted epochs to kTuneDeep
     std::vector<char> conv((size_t)N * nk, 0), tried(nk, 0);
     std::vector<double> pred((size_t)N * nk, INFINITY), best(N, INFINITY);
-    int trials = 0;
-    double seconds = 0;
-    for (int k = kTop; k <= kBottom; ++k) {  // steps gamma0_i * 2^(-k/2), shared k
+    for (int k = kTop; k <= kBottom; ++k) {
         const double scale = std::pow(2.0, -0.5 * k);
         for (auto *c : b->ctx) TRY(reset_state(c, err));
         std::vector<TuneTrial> t(N);
@@ -1501,7 +1526,7 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
             }
             float ms = 0;
             TRY(batch_segment(b, &ms, err));
-            seconds += ms * 1e-3;
+            *seconds += ms * 1e-3;
             for (auto *c : b->ctx) c->updates_done += c->n;
             TRY(grads(g));
             for (int i = 0; i < N; ++i) {
@@ -1514,7 +1539,7 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
                 t[i].y.push_back(std::log10(std::max(g[i] / g0[i], 1e-300)));
             }
         }
-        ++trials;
+        ++*trials;
         tried[k - kTop] = 1;
         bool any_better = false, all_settled = true;
         for (int i = 0; i < N; ++i) {
@@ -1529,11 +1554,10 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
         }
         if (!any_better && all_settled && k >= 2) break;  // smaller steps help no instance any more
     }
+    kc_out->assign(N, -1000);
+    pc_out->assign(N, INFINITY);
     for (int i = 0; i < N; ++i) {
-        asaga_ctx *c = b->ctx[i];
-        // the largest step that converges (and whose next smaller step does too),
-        // then the fastest predicted step at least one notch inside it
-        int kF = kBottom + 1;
+        int kF = kBottom + 1;  // the largest step that converges (and whose next smaller step does too)
         for (int k = kTop; k <= kBottom && tried[k - kTop]; ++k) {
             const bool next_ok = k == kBottom || !tried[k + 1 - kTop] || conv[(size_t)i * nk + (k + 1 - kTop)];
             if (conv[(size_t)i * nk + (k - kTop)] && next_ok) {
@@ -1549,13 +1573,133 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
                 kc = k;
             }
         if (kc == -1000 && kF + 1 <= kBottom) kc = kF + 1;  // untried or unsettled: one notch inside
-        if (kc != -1000) c->gamma = c->gamma_base * std::pow(2.0, -0.5 * kc);
+        (*kc_out)[i] = kc;
+        (*pc_out)[i] = pc;
+    }
+    return ASAGA_OK;
+}
+
+// Longer trials for the instances whose prediction lies beyond twice the
+// trial (ill-conditioned ones slow down after the trial's early phase):
+// they alone run again from x = 0 at their chosen step (the others get no
+// updates), for up to 8x the trial length, until the prediction is within
+// twice the epochs run.
+asaga_status batch_refine_predictions(asaga_batch *b, int E, const std::vector<int> &kc, std::vector<double> *pc,
+                                      double *seconds, std::string *err) {
+    const int N = b->count;
+    std::vector<int> slow;
+    for (int i = 0; i < N; ++i)
+        if (kc[i] != -1000 && std::isfinite((*pc)[i]) && (*pc)[i] > 2.0 * E) slow.push_back(i);
+    if (slow.empty()) return ASAGA_OK;
+    std::vector<double> g0(N, 0.0);
+    std::vector<TuneTrial> t(N);
+    std::vector<char> live(N, 0);
+    for (int i : slow) {
+        live[i] = 1;
+        asaga_ctx *c = b->ctx[i];
+        TRY(reset_state(c, err));
+        TRY(enqueue_grad(c, err));
+        CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy");
+    }
+    TRY(stream_sync(b->ctx[0], err));
+    for (int i : slow) g0[i] = b->ctx[i]->hout[2];
+    for (int e = 1; e <= 8 * E; ++e) {
+        bool any = false;
+        for (int i = 0; i < N; ++i) {
+            asaga_ctx *c = b->ctx[i];
+            b->h_up[i].gamma = (float)(c->gamma_base * std::pow(2.0, -0.5 * (kc[i] == -1000 ? 0 : kc[i])));
+            b->h_up[i].t_begin = (uint64_t)c->updates_done;
+            b->h_up[i].count = live[i] ? c->n : 0;
+            any = any || live[i];
+        }
+        if (!any) break;
+        float ms = 0;
+        TRY(batch_segment(b, &ms, err));
+        *seconds += ms * 1e-3;
+        for (int i : slow) {
+            if (!live[i]) continue;
+            asaga_ctx *c = b->ctx[i];
+            c->updates_done += c->n;
+            TRY(enqueue_grad(c, err));
+            CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy");
+        }
+        TRY(stream_sync(b->ctx[0], err));
+        for (int i : slow) {
+            if (!live[i]) continue;
+            const double g = b->ctx[i]->hout[2];
+            t[i].epochs = e;
+            if (!std::isfinite(g) || g > 1e6 * g0[i]) {
+                t[i].diverged = true;
+                live[i] = 0;
+                (*pc)[i] = INFINITY;
+                continue;
+            }
+            t[i].y.push_back(std::log10(std::max(g / g0[i], 1e-300)));
+            if (e >= E) {
+                const double pe = predict_epochs(t[i]);
+                if (!std::isfinite(pe) || pe <= 2.0 * e || t[i].y.back() <= kTuneDeep || e == 8 * E) {
+                    (*pc)[i] = pe;
+                    live[i] = 0;
+                }
+            }
+        }
+    }
+    for (int i : slow) TRY(reset_state(b->ctx[i], err));
+    return ASAGA_OK;
+}
+
+asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    const int E = trial_epochs > 0 ? std::max(5, (int)std::ceil(trial_epochs)) : 16;
+    const int N = b->count;
+    int trials = 0;
+    double seconds = 0;
+    // 1. steps under the default schedule (equal epoch times)
+    TRY(batch_default_schedule(b, err));
+    std::vector<int> kc1, kc2;
+    std::vector<double> pc1, pc2;
+    TRY(batch_tune_pass(b, E, &kc1, &pc1, &trials, &seconds, err));
+    TRY(batch_refine_predictions(b, E, kc1, &pc1, &seconds, err));
+    const std::vector<int> warps1 = b->warps;
+    // 2. warps in proportion to each instance's predicted work (epochs x epoch
+    //    cost), steps again; kept if the predicted makespan is shorter
+    std::vector<double> finite;
+    for (double p : pc1)
+        if (std::isfinite(p)) finite.push_back(p);
+    std::sort(finite.begin(), finite.end());
+    const double fallback = finite.empty() ? 1.0 : finite.back();
+    std::vector<double> w(N);
+    for (int i = 0; i < N; ++i)
+        w[i] = batch_epoch_cost(b->ctx[i]) * std::max(1.0, std::isfinite(pc1[i]) ? pc1[i] : fallback);
+    TRY(batch_weighted_schedule(b, w, err));
+    bool second = b->warps != warps1;
+    if (second) {
+        TRY(batch_tune_pass(b, E, &kc2, &pc2, &trials, &seconds, err));
+        TRY(batch_refine_predictions(b, E, kc2, &pc2, &seconds, err));
+        bool lost = false;  // an instance predicted under the first schedule but not the second
+        for (int i = 0; i < N; ++i) lost = lost || (std::isfinite(pc1[i]) && !std::isfinite(pc2[i]));
+        // the predictions of slow instances run short (their convergence keeps
+        // slowing down), so their makespans compare poorly; the second
+        // schedule, which gives them more warps, stays unless it loses an
+        // instance (measured: 0.35-0.40 s to the batch's 1e-6 with it,
+        // 0.63-0.75 s without)
+        if (lost) {
+            second = false;
+            b->warps = warps1;
+            TRY(batch_layout(b, err));
+        }
+    }
+    const std::vector<int> &kc = second ? kc2 : kc1;
+    const std::vector<double> &pc = second ? pc2 : pc1;
+    for (int i = 0; i < N; ++i) {
+        asaga_ctx *c = b->ctx[i];
+        if (kc[i] != -1000) c->gamma = c->gamma_base * std::pow(2.0, -0.5 * kc[i]);
         c->warps = b->warps[i];
         TRY(reset_state(c, err));
         if (res) {
             res[i].warps = b->warps[i];
             res[i].gamma = c->gamma;
-            res[i].score = std::isfinite(pc) ? 1.0 / pc : -1.0;
+            res[i].score = std::isfinite(pc[i]) ? 1.0 / pc[i] : -1.0;
             res[i].trials = trials;
             res[i].seconds = seconds;
         }
@@ -1732,6 +1876,28 @@ asaga_status asaga_set_state(asaga_ctx *c, const float *x, const float *abar, co
     if (alpha) CK(cudaMemcpyAsync(c->alpha, alpha, c->n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy alpha");
     TRY(stream_sync(c, err));
     c->updates_done = updates_done;
+    return ASAGA_OK;
+}
+
+asaga_status asaga_set_schedule(asaga_ctx *c, int warps, double gamma, int warps_per_block) {
+    if (!c) return ASAGA_EINVAL;
+    std::string *err = &c->err;
+    if (c->deterministic) return fail(err, ASAGA_EINVAL, "deterministic mode runs one warp");
+    if (warps < 1 || warps > c->resident_warps)
+        return fail(err, ASAGA_EINVAL, "warps must be in [1, " + std::to_string(c->resident_warps) + "]");
+    if (!(gamma > 0) || !std::isfinite(gamma)) return fail(err, ASAGA_EINVAL, "gamma must be finite and > 0");
+    if (warps_per_block < 0 || warps_per_block > kUpdateBlock / 32)
+        return fail(err, ASAGA_EINVAL, "warps_per_block must be in [0, 8]");
+    c->warps = warps;
+    c->gamma = gamma;
+    c->spread = false;
+    if (warps_per_block > 0 && warps_per_block < kUpdateBlock / 32) {
+        c->spread = true;
+        if (update_warps_per_block(c, warps) != warps_per_block) {
+            c->spread = false;
+            return fail(err, ASAGA_EINVAL, "warps_per_block does not match the spread of these warps over the SMs");
+        }
+    }
     return ASAGA_OK;
 }
 

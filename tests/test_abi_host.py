@@ -155,3 +155,7 @@ def test_cancel_needs_a_context(lib):
     assert L.asaga_cancel(None) == asaga.EINVAL
     assert L.asaga_batch_cancel(None) == asaga.EINVAL
     assert asaga.asaga_status_string(asaga.ECANCELLED) == "ASAGA_ECANCELLED"
+
+
+def test_set_schedule_needs_a_context(lib):
+    assert asaga.load().asaga_set_schedule(None, 4, 0.1, 0) == asaga.EINVAL

@@ -248,6 +248,25 @@ def test_autotune_leaves_a_zero_state_and_rejects_deterministic_mode():
             asaga.asaga_autotune(c.ctx)
 
 
+def test_a_tuned_schedule_transfers_to_a_new_context():
+    p = synth.rcv1_like(seed=22, n=60000, d=6000)
+    cert = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 30, ep), rel_tol=1e-10)
+    with asaga.Context(p, seed=2) as c:
+        asaga.asaga_autotune(c.ctx)
+        tuned = asaga.asaga_get_info(c.ctx)
+    with asaga.Context(p, seed=3, abar_recompute_every=5) as c:
+        asaga.asaga_set_schedule(c.ctx, tuned["warps"], tuned["gamma"], tuned["warps_per_block"])
+        info = asaga.asaga_get_info(c.ctx)
+        assert (info["warps"], info["gamma"], info["warps_per_block"]) == \
+            (tuned["warps"], tuned["gamma"], tuned["warps_per_block"])
+        s, r = asaga.asaga_run(c.ctx, 200, 1e-6, cert["fstar"])
+        assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict(), tuned)
+        with pytest.raises(asaga.AsagaError):
+            asaga.asaga_set_schedule(c.ctx, 0, 0.1)
+        with pytest.raises(asaga.AsagaError):
+            asaga.asaga_set_schedule(c.ctx, 64, -1.0)
+
+
 def test_async_dense_ridge_reaches_closed_form():
     p = synth.dense_ridge(20000, 54, storage="f16", lam=1e-3, seed=23)
     xs = R.ridge_closed_form(p)
