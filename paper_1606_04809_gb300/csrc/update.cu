@@ -40,6 +40,11 @@ namespace asaga {
 
 constexpr int kSlots = 4;
 constexpr int kRowCap = 32 * kSlots;  // entries of a row staged in shared memory
+// Entries kRowCap .. kRowCap + 32 kTailSlots - 1 of a long row are loaded
+// from global memory into registers before the update's reads start, so that
+// the read-to-write window holds only their state gathers; entries beyond
+// are read inside the window (rare: rows of more than 256 entries).
+constexpr int kTailSlots = 4;
 constexpr int kStages = 4;            // staged CSR slices per warp (ring)
 constexpr int kMetaRing = 8;          // staged row_ptr / label entries per warp (ring)
 
@@ -167,19 +172,24 @@ __device__ __forceinline__ void stage_slice(const UpdateParams &P, WarpRing &R, 
 // The state-dependent part of one update: the inconsistent reads
 // (begin_update), then the dot product, loss derivative and atomic adds
 // (finish_update).
-template <bool kDense> struct Update {
+// kN register slots of 32 entries: the staged part (kSlots), plus for the
+// single-problem sparse kernel the early-loaded tail of a long row (dense
+// rows, and the batch's short rows, need none).
+template <int kN> struct Update {
     int64_t i, start;
     int len;
     float label, alpha_hat, scale;
-    int c[kSlots];
-    float a[kSlots];
-    float4 s[kSlots];
+    int c[kN];
+    float a[kN];
+    float4 s[kN];
 };
 
-// Reads the staged row and issues the inconsistent reads of x^, abar, D and alpha^_i.
-template <typename T, typename I, bool kDense>
-__device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRing &R, int m, int st, int lane,
-                                             Update<kDense> &u) {
+// The row's data (not the solver state): the staged part from shared memory,
+// the next 32 kTailSlots entries of a long row from global memory.  Runs
+// before the update's reads, outside the window that sets the overlap.
+template <typename T, typename I, bool kDense, int kN>
+__device__ __forceinline__ bool load_row(const UpdateParams &P, const WarpRing &R, int m, int st, int lane,
+                                         Update<kN> &u) {
     u.i = R.row[m];
     u.start = R.start[m];
     const int64_t end = R.end[m];
@@ -188,28 +198,45 @@ __device__ __forceinline__ bool begin_update(const UpdateParams &P, const WarpRi
     u.label = R.label[m];
     u.scale = IsRowScale<T>::value ? R.scale[m] : 0.f;
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) {
+    for (int q = 0; q < kN; ++q) {
         const int k = lane + 32 * q;
         u.c[q] = 0;
         u.a[q] = 0.f;
-        u.s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (k < u.len) {
-            u.c[q] = kDense ? k : staged_col<I>(R.col[st], u.start, k);
-            if constexpr (IsRowScale<T>::value)
-                u.a[q] = u.scale;
-            else
-                u.a[q] = staged_value<T>(R.val[st], u.start, k);
-            u.s[q] = ld_state(P.state + u.c[q] * (int64_t)P.stride);
+            if (q < kSlots) {
+                u.c[q] = kDense ? k : staged_col<I>(R.col[st], u.start, k);
+                if constexpr (IsRowScale<T>::value)
+                    u.a[q] = u.scale;
+                else
+                    u.a[q] = staged_value<T>(R.val[st], u.start, k);
+            } else {
+                u.c[q] = kDense ? k : col_stream<I>(P.col_idx, u.start + k);
+                if constexpr (IsRowScale<T>::value)
+                    u.a[q] = u.scale;
+                else
+                    u.a[q] = to_f32(ld_stream(static_cast<const T *>(P.values) + u.start + k));
+            }
         }
     }
-    u.alpha_hat = __ldcg(P.alpha + u.i);
     return true;
 }
 
+// Issues the inconsistent reads of x^, abar, D (one 16-byte gather per
+// entry) and alpha^_i: the start of the update's window.
+template <int kN>
+__device__ __forceinline__ void begin_update(const UpdateParams &P, int lane, Update<kN> &u) {
+#pragma unroll
+    for (int q = 0; q < kN; ++q) {
+        u.s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane + 32 * q < u.len) u.s[q] = ld_state(P.state + u.c[q] * (int64_t)P.stride);
+    }
+    u.alpha_hat = __ldcg(P.alpha + u.i);
+}
+
 // Dot product, loss derivative and the atomic adds to x, abar and alpha_i.
-// Column and value of entry k >= kRowCap of the update's row (global memory).
-template <typename T, typename I, bool kDense>
-__device__ __forceinline__ void tail_entry(const UpdateParams &P, const Update<kDense> &u, int k, int &col,
+// Column and value of an entry past the register slots (global memory).
+template <typename T, typename I, bool kDense, int kN>
+__device__ __forceinline__ void tail_entry(const UpdateParams &P, const Update<kN> &u, int k, int &col,
                                           float &a) {
     col = kDense ? k : col_stream<I>(P.col_idx, u.start + k);
     if constexpr (IsRowScale<T>::value)
@@ -218,17 +245,17 @@ __device__ __forceinline__ void tail_entry(const UpdateParams &P, const Update<k
         a = to_f32(ld_stream(static_cast<const T *>(P.values) + u.start + k));
 }
 
-template <typename T, typename I, bool kDense>
-__device__ __forceinline__ void finish_update(const UpdateParams &P, const Update<kDense> &u, int lane) {
+template <typename T, typename I, bool kDense, int kN>
+__device__ __forceinline__ void finish_update(const UpdateParams &P, const Update<kN> &u, int lane) {
     const float4 *__restrict__ state = P.state;
     const int64_t stride = P.stride;
     float z = 0.f;
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) z = fmaf(u.a[q], u.s[q].x, z);
-    for (int k = lane + kRowCap; k < u.len; k += 32) {  // rest of a long row
+    for (int q = 0; q < kN; ++q) z = fmaf(u.a[q], u.s[q].x, z);
+    for (int k = lane + 32 * kN; k < u.len; k += 32) {  // rest of a very long row
         int cc;
         float av;
-        tail_entry<T, I, kDense>(P, u, k, cc, av);
+        tail_entry<T, I, kDense, kN>(P, u, k, cc, av);
         z = fmaf(av, ld_state(state + cc * stride).x, z);
     }
     z = warp_sum(z);
@@ -237,7 +264,7 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
     const float gamma = P.gamma, lambda = P.lambda, inv_n = P.inv_n;
     if (P.plain_writes) {  // non-thread-safe x_v = x_v + dx (App. G.2 comparison): concurrent adds can be lost
 #pragma unroll
-        for (int q = 0; q < kSlots; ++q) {
+        for (int q = 0; q < kN; ++q) {
             if (lane + 32 * q < u.len) {
                 const float dx = -gamma * fmaf(delta, u.a[q], u.s[q].z * fmaf(lambda, u.s[q].x, u.s[q].y));
                 float4 *ptr = P.state + u.c[q] * stride;
@@ -249,16 +276,16 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
         return;
     }
 #pragma unroll
-    for (int q = 0; q < kSlots; ++q) {
+    for (int q = 0; q < kN; ++q) {
         if (lane + 32 * q < u.len) {
             const float dx = -gamma * fmaf(delta, u.a[q], u.s[q].z * fmaf(lambda, u.s[q].x, u.s[q].y));
             red_add_v2(P.state + u.c[q] * stride, dx, delta * u.a[q] * inv_n);
         }
     }
-    for (int k = lane + kRowCap; k < u.len; k += 32) {
+    for (int k = lane + 32 * kN; k < u.len; k += 32) {
         int cc;
         float av;
-        tail_entry<T, I, kDense>(P, u, k, cc, av);
+        tail_entry<T, I, kDense, kN>(P, u, k, cc, av);
         const float4 sv = ld_state(state + cc * stride);
         const float dx = -gamma * fmaf(delta, av, sv.z * fmaf(lambda, sv.x, sv.y));
         red_add_v2(P.state + cc * stride, dx, delta * av * inv_n);
@@ -270,7 +297,7 @@ __device__ __forceinline__ void finish_update(const UpdateParams &P, const Updat
 // Iteration k processes the row of update warp + k W; before it, all commit
 // groups but the newest are complete, which covers that row's staged slice
 // and the row_ptr entries of row k + 2, whose slice is requested next.
-template <typename T, typename I, bool kDense>
+template <typename T, typename I, bool kDense, int kN>
 __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R, int warp, int lane) {
     const int64_t W = P.nwarps;
     uint64_t deadline = 0;
@@ -302,11 +329,14 @@ __device__ __forceinline__ void warp_updates(const UpdateParams &P, WarpRing &R,
         stage_meta<T, kDense>(P, R, (int)((k + 4) & (kMetaRing - 1)), more ? row_of(P, warp + (k + 4) * W, bad) : -1,
                            lane);
         cp_async_commit();
+        Update<kN> u;
+        const bool ok = load_row<T, I, kDense, kN>(P, R, m, (int)(k & (kStages - 1)), lane, u);
         uint64_t t_read = 0;
         if (P.trace) t_read = globaltimer_ns();
-        Update<kDense> u;
-        if (begin_update<T, I, kDense>(P, R, m, (int)(k & (kStages - 1)), lane, u))
-            finish_update<T, I, kDense>(P, u, lane);
+        if (ok) {
+            begin_update<kN>(P, lane, u);
+            finish_update<T, I, kDense, kN>(P, u, lane);
+        }
         if (P.trace && lane == 0) {
             P.trace[2 * (warp + k * W)] = t_read;
             P.trace[2 * (warp + k * W) + 1] = globaltimer_ns();
@@ -342,7 +372,7 @@ __global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= P.nwarps) return;
-    warp_updates<T, I, kDense>(P, rings[threadIdx.x >> 5], warp, lane);
+    warp_updates<T, I, kDense, kDense ? kSlots : kSlots + kTailSlots>(P, rings[threadIdx.x >> 5], warp, lane);
 }
 
 // Many independent problems in one launch: block b serves instance
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((blockIdx.x - block_begin[s_inst]) * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= sp.nwarps || sp.count <= 0) return;
-    warp_updates<T, I, kDense>(sp, rings[threadIdx.x >> 5], warp, lane);
+    warp_updates<T, I, kDense, kSlots>(sp, rings[threadIdx.x >> 5], warp, lane);
 }
 
 struct UpdateLaunch {
