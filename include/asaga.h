@@ -408,8 +408,9 @@ asaga_status asaga_batch_cancel(asaga_batch *b);
  * trial runs on alone (up to 8x longer) to refine it.  Two passes: under
  * the default schedule, then with
  * warps in proportion to each instance's predicted work (epochs x epoch
- * cost, within the same caps); the second is kept unless an instance
- * predicted under the first has no prediction under it.  Leaves
+ * cost, within the same caps); the second is kept, except that an
+ * instance predicted under the first but not under the second keeps its
+ * first step at no more warps than the first schedule gave it.  Leaves
  * every instance at x = 0.  results[i] may be NULL; its score is
  * 1 / predicted epochs. */
 asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);

@@ -1676,18 +1676,25 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
     if (second) {
         TRY(batch_tune_pass(b, E, &kc2, &pc2, &trials, &seconds, err));
         TRY(batch_refine_predictions(b, E, kc2, &pc2, &seconds, err));
-        bool lost = false;  // an instance predicted under the first schedule but not the second
-        for (int i = 0; i < N; ++i) lost = lost || (std::isfinite(pc1[i]) && !std::isfinite(pc2[i]));
-        // the predictions of slow instances run short (their convergence keeps
-        // slowing down), so their makespans compare poorly; the second
-        // schedule, which gives them more warps, stays unless it loses an
-        // instance (measured: 0.35-0.40 s to the batch's 1e-6 with it,
-        // 0.63-0.75 s without)
-        if (lost) {
-            second = false;
-            b->warps = warps1;
-            TRY(batch_layout(b, err));
+        // The predictions of slow instances run short (their convergence keeps
+        // slowing down), so makespans compare poorly and the second schedule,
+        // which gives those instances more warps, is kept (measured: 0.33-0.40 s
+        // to the batch's 1e-6 with it, 0.63-0.75 s without).  An instance that
+        // the first pass predicted and the second did not (a trend test that
+        // failed by chance, or a plateau at more warps) keeps its first step at
+        // no more warps than it had then: W gamma stays at or below the point
+        // whose prediction was measured.
+        bool relayout = false;
+        for (int i = 0; i < N; ++i) {
+            if (!std::isfinite(pc1[i]) || std::isfinite(pc2[i])) continue;
+            kc2[i] = kc1[i];
+            pc2[i] = pc1[i];
+            if (b->warps[i] > warps1[i]) {
+                b->warps[i] = warps1[i];
+                relayout = true;
+            }
         }
+        if (relayout) TRY(batch_layout(b, err));
     }
     const std::vector<int> &kc = second ? kc2 : kc1;
     const std::vector<double> &pc = second ? pc2 : pc1;
