@@ -15,6 +15,9 @@ gamma=1/(3L)), with the problem resident in HBM.  The line also reports:
                   -> asaga_destroy);
   roofline        algorithmic HBM bytes of the update kernel per launch over
                   its CUDA-event time, against the measured HBM peak;
+  hotline         the floor that the most frequent column's state line sets
+                  (its L2 slice serialises every update's read and reduction
+                  of it), measured live, against the kernel's epoch time;
   cpu_baseline    the float64 CPU checker on a bounded sample, one host core;
                   beside it (asaga_all_cores) lock-free ASAGA in C on every
                   host core, the paper's own kind of implementation.
@@ -191,6 +194,26 @@ def ncu_summary(workload):
         except Exception:
             pass
     return out
+
+
+def line_floor(p, kernel_ms):
+    """The epoch floor set by the most frequent column's state line.
+
+    Each update whose row holds a column reads that column's 16-byte state and
+    then reduces into it; the line's L2 slice serialises the pairs, so an
+    epoch needs at least (rows holding the most frequent column) x (service
+    time per pair), the latter measured by asaga_probe_line_rate with enough
+    warps to saturate the line.
+    """
+    from paper_1606_04809_gb300 import asaga
+
+    c_max = int(p.n) if p.dense else int(np.bincount(p.col_idx, minlength=p.d).max())
+    warps, pairs = 2048, 500
+    ns = asaga.asaga_probe_line_rate(warps, pairs)
+    floor_ms = c_max * ns * 1e-6
+    return {"bound": "l2_line", "ns_per_pair": ns, "pairs_per_epoch": c_max, "floor_ms": floor_ms,
+            "kernel_ms": kernel_ms, "frac": floor_ms / kernel_ms,
+            "probe": f"asaga_probe_line_rate({warps} warps x {pairs} pairs on one line)"}
 
 
 def update_hbm_bytes(p, storage, info=None):
@@ -544,6 +567,7 @@ def main():
                 "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": upd_ms, "peak_source": peak_kind,
                 "l2_throughput_pct_of_peak_ncu": ncu.get("l2_pct"),
                 "dram_throughput_pct_of_peak_ncu": ncu.get("dram_pct")}
+    hotline = line_floor(p, upd_ms)
 
     # time to 1e-6 from x = 0
     ttt = None
@@ -616,6 +640,7 @@ def main():
             "autotune": tune,
             "e2e": e2e,
             "roofline": roofline,
+            "hotline": hotline,
             "cpu_baseline": cpu,
             "gpu_launches": launches,
             "clocks": clk,

@@ -232,9 +232,9 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  * options.gamma or 1/(3L), k = -3..16 (the largest, 0.94/L, below 1/L).
  * Each trial starts from x = 0,
  * alpha = 0 and records the float64 |grad f|^2 after every epoch:
- *  1. frontier: at min(1024, n/32, resident) warps (Theorem 2 asks for
+ *  1. frontier: at min(1024, n/64, resident) warps (Theorem 2 asks for
  *     tau < n/10, and tau measures 1.5 to 4 times the warps; no candidate
- *     exceeds n/32 warps), bisection over k for the
+ *     exceeds n/64 warps), bisection over k for the
  *     largest step whose 16-epoch trial converges (|grad f|^2 shrinks by
  *     1e6, or its log falls with a least-squares t-statistic >= 3.5);
  *     if none does, again with 8x fewer warps (twice at most);
@@ -304,6 +304,20 @@ typedef struct {
  * than 2 updates, out NULL. */
 asaga_status asaga_measure_overlap(asaga_ctx *ctx, double epochs, asaga_overlap *out);
 
+/* Service time of one column's state line under the update's access
+ * pattern: the 16-byte read of {x^_v, abar_v, D_v} and then the 2-wide float
+ * reduction into x_v and abar_v that depends on it (Algorithm 2's read of x^
+ * and write of x and abar, for one column v).  `warps` warps each repeat the
+ * pair `pairs` times on one line; *ns_per_pair = elapsed device time /
+ * (warps x pairs).  With enough warps the line saturates and this is the
+ * time its L2 slice takes per pair, so a problem whose most frequent column
+ * is in c rows needs at least c x ns_per_pair per epoch (the update kernel's
+ * roofline when that column is in most rows).  Allocates and frees 256 bytes
+ * of device memory and a stream on the current device, and waits for the
+ * probe.  EINVAL: warps outside [1, 65536], pairs < 1, ns_per_pair NULL
+ * (asaga_last_error(NULL) says which); ECUDA: a CUDA error. */
+asaga_status asaga_probe_line_rate(int warps, int64_t pairs, double *ns_per_pair);
+
 /* Deterministic replay: runs one update per entry of idx (row indices in
  * [0,n)), strictly in order, on a single warp.  idx is a host pointer if
  * idx_on_device = 0, else a device pointer.  This is the serial Sparse SAGA
@@ -348,8 +362,8 @@ asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
 asaga_status asaga_set_schedule(asaga_ctx *ctx, int warps, double gamma, int warps_per_block);
 
 /* Reason for the last failure of a call on ctx (or, when ctx is NULL, of
- * the calling thread's last asaga_create, asaga_sample_rows or
- * asaga_recompute_abar_noalloc); never NULL. */
+ * the calling thread's last asaga_create, asaga_sample_rows,
+ * asaga_probe_line_rate or asaga_recompute_abar_noalloc); never NULL. */
 const char *asaga_last_error(const asaga_ctx *ctx);
 
 const char *asaga_status_string(asaga_status s);
@@ -372,7 +386,7 @@ typedef struct asaga_batch asaga_batch;
  * options[0].abar_recompute_every, and run on options[0].cuda_stream.  The
  * initial schedule gives instance i warps in proportion to n_i (1 + k_i/128),
  * k_i its mean row length (an update's cost is mostly a fixed latency; a
- * multiple of 4, at least 4, at most max(4, n_i/32), which keeps tau near
+ * multiple of 4, at least 4, at most max(4, n_i/64), which keeps tau below
  * n_i/10 as Theorem 2 asks) within the warps that
  * can be resident at once.  EINVAL as asaga_create, or for mixed dtypes or
  * layouts, deterministic options, or count < 1. */

@@ -131,6 +131,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_recompute_abar_noalloc.restype = i32
     L.asaga_sample_rows.argtypes = [ctypes.c_uint64, i64, i32, ctypes.c_uint64, i64, vp]
     L.asaga_sample_rows.restype = i32
+    L.asaga_probe_line_rate.argtypes = [i32, i64, P(dbl)]
+    L.asaga_probe_line_rate.restype = i32
     L.asaga_cancel.argtypes = [vp]
     L.asaga_cancel.restype = i32
     L.asaga_set_schedule.argtypes = [vp, i32, dbl, i32]
@@ -312,6 +314,13 @@ def asaga_sample_rows(seed: int, n: int, t_begin: int, count: int, sampling="uni
     s = load().asaga_sample_rows(int(seed), int(n), smp, int(t_begin), int(count), _ptr(rows) if count else None)
     _check(None, s)
     return rows
+
+
+def asaga_probe_line_rate(warps: int, pairs: int) -> float:
+    """Device ns per (16-byte read, dependent 2-wide reduction) pair on one state line."""
+    ns = ctypes.c_double()
+    _check(None, load().asaga_probe_line_rate(int(warps), int(pairs), ctypes.byref(ns)))
+    return ns.value
 
 
 def asaga_get_state(ctx: int):

@@ -940,8 +940,8 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     constexpr int kTop = -3, kBottom = 16;
     auto step = [&](int k) { return c->gamma_base * std::pow(2.0, -0.5 * k); };
     // Theorem 2 wants the overlap tau below n/10; measured, tau is 1.5 to 4
-    // times the number of warps: at most n/32 warps
-    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 32));
+    // times the number of warps: at most n/64 warps keeps tau below n/16
+    const int64_t cap = std::max<int64_t>(1, std::min<int64_t>(c->resident_warps, c->n / 64));
     asaga_tune_result r;
     std::memset(&r, 0, sizeof(r));
     r.warps = c->warps;
@@ -1246,7 +1246,7 @@ double batch_epoch_cost(const asaga_ctx *c) {
 }
 
 // Warps in proportion to weight[i] (a multiple of 4, at least 4, at most
-// max(4, n_i/32) so that tau stays near n_i/10 as Theorem 2 asks), within
+// max(4, n_i/64) so that tau stays below n_i/10 as Theorem 2 asks), within
 // the warps that can be resident at once.
 asaga_status batch_weighted_schedule(asaga_batch *b, const std::vector<double> &weight, std::string *err) {
     const int64_t budget = (int64_t)b->resident_blocks * 4;
@@ -1258,7 +1258,7 @@ asaga_status batch_weighted_schedule(asaga_batch *b, const std::vector<double> &
         const asaga_ctx *c = b->ctx[i];
         const double share = total > 0 ? weight[i] / total * (double)budget : 4.0;
         int64_t w = std::max<int64_t>(4, ((int64_t)share / 4) * 4);
-        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 32 / 4) * 4));
+        w = std::min<int64_t>(w, std::max<int64_t>(4, (c->n / 64 / 4) * 4));
         b->warps[i] = (int)w;
         used += w;
     }

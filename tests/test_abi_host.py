@@ -159,3 +159,15 @@ def test_cancel_needs_a_context(lib):
 
 def test_set_schedule_needs_a_context(lib):
     assert asaga.load().asaga_set_schedule(None, 4, 0.1, 0) == asaga.EINVAL
+
+
+def test_line_probe_arguments_are_checked_before_any_cuda_call(lib):
+    import ctypes
+
+    L = asaga.load()
+    ns = ctypes.c_double()
+    assert L.asaga_probe_line_rate(0, 10, ctypes.byref(ns)) == asaga.EINVAL
+    assert "warps must be" in asaga.asaga_last_error(None)
+    assert L.asaga_probe_line_rate(70000, 10, ctypes.byref(ns)) == asaga.EINVAL
+    assert L.asaga_probe_line_rate(4, 0, ctypes.byref(ns)) == asaga.EINVAL
+    assert L.asaga_probe_line_rate(4, 10, None) == asaga.EINVAL
