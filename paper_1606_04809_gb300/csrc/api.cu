@@ -147,15 +147,64 @@ size_t dtype_size(int dt) {
     }
 }
 
-bool value_finite(const void *vals, int dt, int64_t k) {
+// First non-finite value among entries [a, b) of an array of dtype dt, or -1
+// (one tight loop per type; the 16-bit types by their exponent bits).
+int64_t first_nonfinite(const void *vals, int dt, int64_t a, int64_t b) {
     switch (dt) {
-    case ASAGA_F64: return std::isfinite(((const double *)vals)[k]);
-    case ASAGA_F32: return std::isfinite(((const float *)vals)[k]);
-    case ASAGA_BF16: return (((const uint16_t *)vals)[k] & 0x7F80u) != 0x7F80u;
-    case ASAGA_F16: return (((const uint16_t *)vals)[k] & 0x7C00u) != 0x7C00u;
-    default: return false;
+    case ASAGA_F64:
+        for (int64_t k = a; k < b; ++k)
+            if (!std::isfinite(((const double *)vals)[k])) return k;
+        return -1;
+    case ASAGA_F32:
+        for (int64_t k = a; k < b; ++k)
+            if (!std::isfinite(((const float *)vals)[k])) return k;
+        return -1;
+    case ASAGA_BF16:
+        for (int64_t k = a; k < b; ++k)
+            if ((((const uint16_t *)vals)[k] & 0x7F80u) == 0x7F80u) return k;
+        return -1;
+    case ASAGA_F16:
+        for (int64_t k = a; k < b; ++k)
+            if ((((const uint16_t *)vals)[k] & 0x7C00u) == 0x7C00u) return k;
+        return -1;
+    default: return a < b ? a : -1;
     }
 }
+
+// Repeated-column check of one row at a time: an open-addressing set of the
+// row's columns whose slots carry the row's stamp, so stale slots of earlier
+// rows count as empty and nothing is cleared between rows.  Sized to at
+// least twice the row (so it stays in L1 for ordinary rows, whatever d is).
+class RowColumnSet {
+  public:
+    // Starts a row of len entries.
+    void begin(int64_t len) {
+        size_t cap = 64;
+        while ((int64_t)cap < 2 * len) cap <<= 1;
+        if (slot_.size() < cap) slot_.assign(cap, 0);
+        mask_ = (uint32_t)(cap - 1);
+        if (++stamp_ == 0) {  // the stamp wrapped: every slot is stale by clearing
+            std::fill(slot_.begin(), slot_.end(), 0);
+            stamp_ = 1;
+        }
+    }
+    // False if c is already in the row.
+    bool insert(int32_t c) {
+        const uint64_t tagged = ((uint64_t)stamp_ << 32) | (uint32_t)c;
+        uint32_t h = ((uint32_t)c * 2654435761u) & mask_;
+        while ((uint32_t)(slot_[h] >> 32) == stamp_) {
+            if (slot_[h] == tagged) return false;
+            h = (h + 1) & mask_;
+        }
+        slot_[h] = tagged;
+        return true;
+    }
+
+  private:
+    std::vector<uint64_t> slot_;
+    uint32_t mask_ = 0;
+    uint32_t stamp_ = 0;
+};
 
 template <typename T>
 asaga_status dev_alloc(T **p, size_t count, asaga_ctx *c, std::string *err, const char *what) {
@@ -204,9 +253,8 @@ bool parallel_check(int64_t count, int64_t min_chunk, int max_threads, F body, s
     return true;
 }
 
-// Host-side validation of the problem (copies device inputs to the host
-// first).  Fills max_row_len.
-asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *max_row_len, std::string *err) {
+// Checks of the problem and options that need no pass over the data.
+asaga_status validate_args(const asaga_problem *p, const asaga_options *o, std::string *err) {
     if (!p || !o) return fail(err, ASAGA_EINVAL, "problem or options is NULL");
     if (p->n < 1 || p->d < 1) return fail(err, ASAGA_EINVAL, "n and d must be >= 1");
     if (p->d > (int64_t)INT32_MAX) return fail(err, ASAGA_EINVAL, "d must fit in int32");
@@ -225,15 +273,26 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
     if (o->sampling == ASAGA_SAMPLE_PERMUTATION && p->n > ((int64_t)1 << 62))
         return fail(err, ASAGA_EINVAL, "permutation sampling needs n <= 2^62");
     if (!p->values || !p->labels) return fail(err, ASAGA_EINVAL, "values or labels is NULL");
-    int64_t nnz = p->nnz;
     if (p->dense) {
         if (p->d > 0 && p->n > INT64_MAX / p->d) return fail(err, ASAGA_EINVAL, "n*d overflows");
-        if (nnz != 0 && nnz != p->n * p->d) return fail(err, ASAGA_EINVAL, "dense problem needs nnz = n*d (or 0)");
-        nnz = p->n * p->d;
+        if (p->nnz != 0 && p->nnz != p->n * p->d)
+            return fail(err, ASAGA_EINVAL, "dense problem needs nnz = n*d (or 0)");
     } else {
-        if (nnz < 0) return fail(err, ASAGA_EINVAL, "nnz < 0");
-        if (!p->row_ptr || (!p->col_idx && nnz > 0)) return fail(err, ASAGA_EINVAL, "row_ptr or col_idx is NULL");
+        if (p->nnz < 0) return fail(err, ASAGA_EINVAL, "nnz < 0");
+        if (!p->row_ptr || (!p->col_idx && p->nnz > 0)) return fail(err, ASAGA_EINVAL, "row_ptr or col_idx is NULL");
     }
+    return ASAGA_OK;
+}
+
+// One pass over the rows on host threads (device inputs are copied to the
+// host first): labels finite (and +-1 for logistic), row_ptr from 0 to nnz
+// and non-decreasing, columns in [0, d) and not repeated within a row, values
+// finite.  Threads take contiguous blocks of rows and the error reported is
+// the one of the first bad row.  Fills max_row_len.  Call after
+// validate_args.
+asaga_status validate_content(const asaga_problem *p, const asaga_options *o, int64_t *max_row_len,
+                              std::string *err) {
+    const int64_t nnz = p->dense ? p->n * p->d : p->nnz;
     const size_t vsz = dtype_size(p->values_dtype);
     std::vector<int64_t> rp_h;
     std::vector<int32_t> ci_h;
@@ -267,53 +326,62 @@ asaga_status validate(const asaga_problem *p, const asaga_options *o, int64_t *m
             ci = ci_h.data();
         }
     }
-    std::string msg;
+    if (!p->dense && (rp[0] != 0 || rp[p->n] != nnz))
+        return fail(err, ASAGA_EINVAL, "row_ptr must start at 0 and end at nnz");
     const int loss = o->loss;
-    if (!parallel_check(p->n, 1 << 16, 32, [&](int64_t lo, int64_t hi, std::string *e) {
+    const int vdt = p->values_dtype;
+    const int64_t d = p->d;
+    const bool dense = p->dense != 0;
+    int64_t mrl = dense ? d : 0;
+    std::string msg;
+    // repeated columns: up to 2^18 columns each thread stamps a d-sized array
+    // with the row (it stays in a core's L2); beyond, a per-row set
+    const bool stamps = !dense && d <= (1 << 18);
+    if (!parallel_check(p->n, 1 << 14, 32, [&](int64_t lo, int64_t hi, std::string *e) {
+            RowColumnSet seen;
+            std::vector<uint32_t> stamp(stamps ? d : 0, 0);
+            int64_t m = 0;
             for (int64_t i = lo; i < hi; ++i) {
                 if (!std::isfinite(lab[i])) return void(*e = "non-finite label at row " + std::to_string(i));
                 if (loss == ASAGA_LOSS_LOGISTIC && lab[i] != 1.0 && lab[i] != -1.0)
                     return void(*e = "logistic label not +-1 at row " + std::to_string(i));
-            }
-        }, &msg))
-        return fail(err, ASAGA_EINVAL, msg);
-    const int vdt = p->values_dtype;
-    if (!parallel_check(nnz, 1 << 20, 32, [&](int64_t lo, int64_t hi, std::string *e) {
-            for (int64_t k = lo; k < hi; ++k)
-                if (!value_finite(val, vdt, k)) return void(*e = "non-finite value at entry " + std::to_string(k));
-        }, &msg))
-        return fail(err, ASAGA_EINVAL, msg);
-    int64_t mrl = 0;
-    if (p->dense) {
-        mrl = p->d;
-    } else {
-        if (rp[0] != 0 || rp[p->n] != nnz) return fail(err, ASAGA_EINVAL, "row_ptr must start at 0 and end at nnz");
-        // each thread checks a contiguous block of rows with its own column
-        // stamps (row number within the block + 1), bounded to 256 MB in all
-        const int64_t d = p->d;
-        const int max_threads = (int)std::max<int64_t>(1, std::min<int64_t>(32, (int64_t(256) << 20) / (4 * d)));
-        if (!parallel_check(p->n, 1 << 14, max_threads, [&](int64_t lo, int64_t hi, std::string *e) {
-                std::vector<uint32_t> stamp(d, 0);
-                int64_t m = 0;
-                for (int64_t i = lo; i < hi; ++i) {
-                    if (rp[i + 1] < rp[i]) return void(*e = "row_ptr decreases at row " + std::to_string(i));
-                    const int64_t len = rp[i + 1] - rp[i];
+                int64_t a = i * d, b = (i + 1) * d;
+                if (!dense) {
+                    // a bad range is reported before anything in it is read
+                    if (rp[i] < 0 || rp[i + 1] < rp[i])
+                        return void(*e = "row_ptr decreases at row " + std::to_string(i));
+                    if (rp[i + 1] > nnz) return void(*e = "row_ptr passes nnz at row " + std::to_string(i));
+                    a = rp[i];
+                    b = rp[i + 1];
+                    const int64_t len = b - a;
                     if (len > INT32_MAX) return void(*e = "row too long");
                     m = len > m ? len : m;
-                    const uint32_t tag = (uint32_t)(i - lo + 1);
-                    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-                        const int32_t c = ci[k];
-                        if (c < 0 || c >= d)
-                            return void(*e = "column index out of range at entry " + std::to_string(k));
-                        if (stamp[c] == tag) return void(*e = "repeated column in row " + std::to_string(i));
-                        stamp[c] = tag;
+                    if (stamps) {
+                        const uint32_t tag = (uint32_t)(i - lo + 1);
+                        for (int64_t k = a; k < b; ++k) {
+                            const int32_t c = ci[k];
+                            if (c < 0 || c >= d)
+                                return void(*e = "column index out of range at entry " + std::to_string(k));
+                            if (stamp[c] == tag) return void(*e = "repeated column in row " + std::to_string(i));
+                            stamp[c] = tag;
+                        }
+                    } else {
+                        seen.begin(len);
+                        for (int64_t k = a; k < b; ++k) {
+                            const int32_t c = ci[k];
+                            if (c < 0 || c >= d)
+                                return void(*e = "column index out of range at entry " + std::to_string(k));
+                            if (!seen.insert(c)) return void(*e = "repeated column in row " + std::to_string(i));
+                        }
                     }
                 }
-                std::lock_guard<std::mutex> g(g_max_mutex);
-                mrl = m > mrl ? m : mrl;
-            }, &msg))
-            return fail(err, ASAGA_EINVAL, msg);
-    }
+                const int64_t bad = first_nonfinite(val, vdt, a, b);
+                if (bad >= 0) return void(*e = "non-finite value at entry " + std::to_string(bad));
+            }
+            std::lock_guard<std::mutex> g(g_max_mutex);
+            mrl = m > mrl ? m : mrl;
+        }, &msg))
+        return fail(err, ASAGA_EINVAL, msg);
     *max_row_len = mrl;
     return ASAGA_OK;
 }
@@ -389,9 +457,10 @@ asaga_status select_hot_columns(asaga_ctx *c, const std::vector<int> &count, std
     TRY(dev_alloc(&c->hot_slot, c->d, c, err, "alloc hot slots"));
     TRY(dev_alloc(&c->hot_col, c->n_hot, c, err, "alloc hot columns"));
     CK(cudaMemcpyAsync(c->hot_slot, slot.data(), c->d * sizeof(int), cudaMemcpyHostToDevice, c->stream), "copy slots");
+    // copies from pageable memory: the host vectors may go once the calls return
     CK(cudaMemcpyAsync(c->hot_col, cand.data(), c->n_hot * sizeof(int), cudaMemcpyHostToDevice, c->stream),
        "copy hot columns");
-    return stream_sync(c, err);
+    return ASAGA_OK;
 }
 
 // Compact layouts of A, applied after the set-up (D, L and the frequent
@@ -444,10 +513,10 @@ asaga_status apply_compact(asaga_ctx *c, bool rows_equal, bool idx16, std::strin
     return ASAGA_OK;
 }
 
-asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
-    NvtxRange range("asaga_create");
-    int64_t mrl = 0;
-    TRY(validate(p, o, &mrl, err));
+// Device set-up, allocations and the copies of the problem: nothing here
+// reads the data by its content (no kernel indexes by a column), so it may
+// run while the content check is still going on.
+asaga_status create_buffers(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
     CK(cudaGetDevice(&c->device), "cudaGetDevice");
     cudaDeviceProp prop;
     CK(cudaGetDeviceProperties(&prop, c->device), "cudaGetDeviceProperties");
@@ -464,7 +533,6 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     c->d = p->d;
     c->dense = p->dense != 0;
     c->nnz = c->dense ? p->n * p->d : p->nnz;
-    c->max_row_len = mrl;
     c->loss = o->loss;
     c->vtype = o->storage_dtype == ASAGA_F32 ? kF32 : (o->storage_dtype == ASAGA_BF16 ? kBF16 : kF16);
     c->lambda = o->lambda;
@@ -535,13 +603,20 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     *c->h_cancel = 0;
     CK(cudaHostGetDevicePointer((void **)&c->d_cancel, c->h_cancel, 0), "cancel flag address");
 
+    return ASAGA_OK;
+}
+
+// D from the column counts, L, gamma and the frequent columns of the
+// evaluation kernels.  Safe on a problem not yet checked: the kernels skip
+// out-of-range columns and row ranges.
+asaga_status create_setup(asaga_ctx *c, const asaga_options *o, std::string *err) {
     // D from the column counts (Sec. 2); dense rows give D = 1
     int *count = nullptr;
     std::vector<int> count_h;
     if (!c->dense) {
         CK(cudaMallocAsync((void **)&count, c->d * sizeof(int), c->stream), "alloc counts");
         CK(cudaMemsetAsync(count, 0, c->d * sizeof(int), c->stream), "memset counts");
-        CK(launch_count_columns(c->col_idx, c->nnz, count, c->stream), "count kernel");
+        CK(launch_count_columns(c->col_idx, c->nnz, c->d, count, c->stream), "count kernel");
         ++c->launches;
     }
     CK(launch_init_state(c->state, c->stride, c->d, count, c->n, c->stream), "init state");
@@ -555,7 +630,7 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
     // L = max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) on the stored values
     const double cl = c->loss == ASAGA_LOSS_LOGISTIC ? 0.25 : 1.0;
     const EvalParams e = eval_params(c);
-    CK(launch_max_row_smoothness(e, c->vtype, c->dense, cl, c->eval_grid, c->partial, c->dout, c->stream),
+    CK(launch_max_row_smoothness(e, c->nnz, c->vtype, c->dense, cl, c->eval_grid, c->partial, c->dout, c->stream),
        "smoothness kernel");
     c->launches += 2;
     CK(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy L");
@@ -570,6 +645,49 @@ asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_optio
         c->delta = (double)mx / (double)c->n;
     }
     if (!c->dense) TRY(select_hot_columns(c, count_h, err));
+    return ASAGA_OK;
+}
+
+// The content check of a problem in host memory, on its own thread while
+// create_buffers allocates and copies; joined (also on every early return)
+// before anything reads the data by content.
+struct ContentCheck {
+    std::thread th;
+    asaga_status status = ASAGA_OK;
+    std::string msg;
+    int64_t max_row_len = 0;
+    void start(const asaga_problem *p, const asaga_options *o) {
+        th = std::thread([this, p, o] { status = validate_content(p, o, &max_row_len, &msg); });
+    }
+    void join() {
+        if (th.joinable()) th.join();
+    }
+    ~ContentCheck() { join(); }
+};
+
+asaga_status create_impl(asaga_ctx *c, const asaga_problem *p, const asaga_options *o, std::string *err) {
+    NvtxRange range("asaga_create");
+    TRY(validate_args(p, o, err));
+    int64_t mrl = 0;
+    ContentCheck check;
+    if (p->on_device) {
+        TRY(validate_content(p, o, &mrl, err));  // reads device memory: before the set-up
+    } else {
+        check.start(p, o);
+    }
+    // The set-up kernels bound every index they read, so they run on the
+    // copied problem while the content check is still looking at it; a
+    // problem that the check rejects only leaves results that are dropped.
+    asaga_status made = create_buffers(c, p, o, err);
+    if (made == ASAGA_OK) made = create_setup(c, o, err);
+    if (!p->on_device) {
+        check.join();
+        // a bad problem is reported as such, even when the device set-up failed too
+        if (check.status != ASAGA_OK) return fail(err, check.status, check.msg);
+        mrl = check.max_row_len;
+    }
+    if (made != ASAGA_OK) return made;
+    c->max_row_len = mrl;
     c->layout = c->vtype;
     if (o->compact && !c->dense) {
         bool rows_equal = false;

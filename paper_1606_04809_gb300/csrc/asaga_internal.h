@@ -113,14 +113,15 @@ cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double
 cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out,
                                    cudaStream_t s);
 
-// prep (eval.cu)
-cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s);
+// prep (eval.cu).  These run while the host is still checking the problem,
+// so they skip columns outside [0, d) and row ranges outside [0, nnz].
+cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int64_t d, int *count, cudaStream_t s);
 // state[v] <- {0, 0, D_v, 0}, D_v = n/count_v (0 if count_v = 0); count may be nullptr (dense: D = 1).
 cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n,
                               cudaStream_t s);
 // out[0] <- max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) (float64) over the stored
 // values; needs D in state.z.  Set-up layout: int32 columns, one value per entry.
-cudaError_t launch_max_row_smoothness(const EvalParams &p, int vtype, bool dense, double c_loss, int grid,
+cudaError_t launch_max_row_smoothness(const EvalParams &p, int64_t nnz, int vtype, bool dense, double c_loss, int grid,
                                       double *partial, double *out, cudaStream_t s);
 // dst (vtype) <- src (src_dtype: 0 f64, 1 f32, 2 bf16, 3 f16), count elements.
 cudaError_t launch_convert(const void *src, int src_dtype, void *dst, int vtype, int64_t count,

@@ -240,9 +240,43 @@ __global__ void reduce_partials_kernel(const double *partial, int grid, int mode
 
 // ------------------------------------------------------------------ set-up
 
-__global__ void count_columns_kernel(const int32_t *col, int64_t nnz, int *count) {
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(count + col[k], 1);
+// Column counts.  A column in most rows would take one global atomic per
+// row on a single address; instead each block counts into a shared-memory
+// open-addressing table (kCountSlots slots, 4 linear probes, a slot's key is
+// written once) and adds its totals to global memory at the end.  An entry
+// whose probes all hold other columns goes straight to global memory.
+// Columns outside [0, d) are skipped: the kernel runs while the host is still
+// checking the problem.
+constexpr int kCountSlots = 4096;
+constexpr int kCountBlocks = 1216;  // 152 SMs x 8 blocks of 256 threads
+__global__ void __launch_bounds__(256) count_columns_kernel(const int32_t *col, int64_t nnz, int64_t d, int *count) {
+    __shared__ int key[kCountSlots];
+    __shared__ int cnt[kCountSlots];
+    for (int j = threadIdx.x; j < kCountSlots; j += blockDim.x) {
+        key[j] = -1;
+        cnt[j] = 0;
+    }
+    __syncthreads();
+    volatile int *vkey = key;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = col[k];
+        if (c < 0 || c >= d) continue;
+        const unsigned h = ((unsigned)c * 2654435761u) >> 20;  // 12 bits (Knuth's multiplicative hash)
+        bool done = false;
+        for (int probe = 0; probe < 4 && !done; ++probe) {
+            const int slot = (int)((h + probe) & (kCountSlots - 1));
+            int kv = vkey[slot];
+            if (kv == -1) kv = atomicCAS(&key[slot], -1, c);  // the key before this thread's attempt
+            if (kv == -1 || kv == c) {
+                atomicAdd(&cnt[slot], 1);
+                done = true;
+            }
+        }
+        if (!done) atomicAdd(count + c, 1);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < kCountSlots; j += blockDim.x)
+        if (key[j] >= 0 && cnt[j] > 0) atomicAdd(count + key[j], cnt[j]);
 }
 
 __global__ void init_state_kernel(float4 *state, int stride, int64_t d, const int *count, int64_t n) {
@@ -255,9 +289,11 @@ __global__ void init_state_kernel(float4 *state, int stride, int64_t d, const in
 
 // Per row: c |a_i|^2 + lambda max_{v in S_i} D_v (the smoothness constant of
 // the component the sparse update samples, with the projected l2 term);
-// partial[b] <- the block's maximum.
+// partial[b] <- the block's maximum.  Rows whose range leaves [0, nnz] and
+// columns outside [0, d) are skipped: the kernel runs while the host is still
+// checking the problem.
 template <typename T, bool kDense>
-__global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalParams P, double c_loss,
+__global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalParams P, int64_t nnz, double c_loss,
                                                                     double *partial) {
     const T *vals = static_cast<const T *>(P.values);
     const int lane = threadIdx.x & 31;
@@ -268,12 +304,20 @@ __global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalPa
     for (int64_t i = gw; i < P.n; i += tw) {
         int64_t start;
         int len;
-        row_range<T, kDense>(P, i, start, len);
+        if (kDense) {
+            start = i * P.d;
+            len = (int)P.d;
+        } else {
+            start = P.row_ptr[i];
+            const int64_t end = P.row_ptr[i + 1];
+            len = (start < 0 || end < start || end > nnz || end - start > INT32_MAX) ? 0 : (int)(end - start);
+        }
         double s = 0.0, dmax = 0.0;
         for (int k = lane; k < len; k += 32) {
             const double a = (double)to_f32(vals[start + k]);
             s += a * a;
             const int c = kDense ? k : static_cast<const int32_t *>(P.col_idx)[start + k];
+            if (c < 0 || c >= P.d) continue;
             dmax = fmax(dmax, (double)ld_state_ro(P.state + (int64_t)c * P.stride).z);
         }
         best = fmax(best, c_loss * warp_sum(s) + P.lambda * warp_max(dmax));
@@ -394,8 +438,11 @@ cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, do
     return cudaGetLastError();
 }
 
-cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int *count, cudaStream_t s) {
-    if (nnz > 0) count_columns_kernel<<<elementwise_grid(nnz), 256, 0, s>>>(col_idx, nnz, count);
+cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int64_t d, int *count, cudaStream_t s) {
+    if (nnz > 0) {
+        const int grid = (int)std::min<int64_t>(kCountBlocks, (nnz + 255) / 256);
+        count_columns_kernel<<<grid, 256, 0, s>>>(col_idx, nnz, d, count);
+    }
     return cudaGetLastError();
 }
 
@@ -405,16 +452,16 @@ cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *c
 }
 
 template <typename T, bool kDense>
-static void smooth_t(const EvalParams &p, double c_loss, int grid, double *partial, cudaStream_t s) {
-    row_smoothness_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, c_loss, partial);
+static void smooth_t(const EvalParams &p, int64_t nnz, double c_loss, int grid, double *partial, cudaStream_t s) {
+    row_smoothness_kernel<T, kDense><<<grid, kEvalBlock, 0, s>>>(p, nnz, c_loss, partial);
 }
 
-cudaError_t launch_max_row_smoothness(const EvalParams &p, int vtype, bool dense, double c_loss, int grid,
+cudaError_t launch_max_row_smoothness(const EvalParams &p, int64_t nnz, int vtype, bool dense, double c_loss, int grid,
                                       double *partial, double *out, cudaStream_t s) {
     switch (vtype) {
-    case kF32: dense ? smooth_t<float, true>(p, c_loss, grid, partial, s) : smooth_t<float, false>(p, c_loss, grid, partial, s); break;
-    case kBF16: dense ? smooth_t<__nv_bfloat16, true>(p, c_loss, grid, partial, s) : smooth_t<__nv_bfloat16, false>(p, c_loss, grid, partial, s); break;
-    case kF16: dense ? smooth_t<__half, true>(p, c_loss, grid, partial, s) : smooth_t<__half, false>(p, c_loss, grid, partial, s); break;
+    case kF32: dense ? smooth_t<float, true>(p, nnz, c_loss, grid, partial, s) : smooth_t<float, false>(p, nnz, c_loss, grid, partial, s); break;
+    case kBF16: dense ? smooth_t<__nv_bfloat16, true>(p, nnz, c_loss, grid, partial, s) : smooth_t<__nv_bfloat16, false>(p, nnz, c_loss, grid, partial, s); break;
+    case kF16: dense ? smooth_t<__half, true>(p, nnz, c_loss, grid, partial, s) : smooth_t<__half, false>(p, nnz, c_loss, grid, partial, s); break;
     default: return cudaErrorInvalidValue;
     }
     cudaError_t e = cudaGetLastError();

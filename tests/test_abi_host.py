@@ -53,6 +53,7 @@ def create(row_ptr, col_idx, values, labels, n=3, d=4, dtype="f64", dense=False,
 
 @pytest.mark.parametrize("mutate,msg", [
     (lambda a: a[0].__setitem__(2, 1), "decreases"),
+    (lambda a: a[0].__setitem__(1, 9), "passes nnz at row 0"),  # row 0 would run past col_idx
     (lambda a: a[0].__setitem__(3, 4), "end at nnz"),
     (lambda a: a[1].__setitem__(1, 4), "out of range"),
     (lambda a: a[1].__setitem__(1, -1), "out of range"),
