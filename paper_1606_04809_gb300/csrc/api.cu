@@ -356,7 +356,14 @@ asaga_status validate_content(const asaga_problem *p, const asaga_options *o, in
                     const int64_t len = b - a;
                     if (len > INT32_MAX) return void(*e = "row too long");
                     m = len > m ? len : m;
-                    if (stamps) {
+                    // the usual case, columns in increasing order: no repeats, and the
+                    // range follows from the first and last (checked without the
+                    // random access of the general check, which other rows take)
+                    bool sorted = len == 0 || (ci[a] >= 0 && ci[b - 1] < d);
+                    for (int64_t k = a + 1; sorted && k < b; ++k) sorted = ci[k] > ci[k - 1];
+                    if (sorted) {
+                        // nothing more to check for the columns
+                    } else if (stamps) {
                         const uint32_t tag = (uint32_t)(i - lo + 1);
                         for (int64_t k = a; k < b; ++k) {
                             const int32_t c = ci[k];

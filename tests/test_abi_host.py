@@ -172,3 +172,25 @@ def test_line_probe_arguments_are_checked_before_any_cuda_call(lib):
     assert L.asaga_probe_line_rate(70000, 10, ctypes.byref(ns)) == asaga.EINVAL
     assert L.asaga_probe_line_rate(4, 0, ctypes.byref(ns)) == asaga.EINVAL
     assert L.asaga_probe_line_rate(4, 10, None) == asaga.EINVAL
+
+
+def test_rows_in_any_column_order_are_checked_alike(lib):
+    """Increasing rows take a fast path; other rows the general check, with the same verdicts."""
+    g = np.random.default_rng(1)
+    n, d, k = 50_000, 3000, 6
+    col = np.stack([g.choice(d, k, replace=False) for _ in range(n)]).astype(np.int32)  # unsorted, distinct
+    row_ptr = np.arange(n + 1, dtype=np.int64) * k
+    vals = np.ones(n * k)
+    y = np.ones(n)
+    assert create(row_ptr, col.ravel(), vals, y, n=n, d=d)[0] != asaga.EINVAL
+    srt = np.sort(col, axis=1)
+    assert create(row_ptr, srt.ravel(), vals, y, n=n, d=d)[0] != asaga.EINVAL
+    for c in (col, srt):
+        bad = c.copy()
+        bad[30_000, 4] = bad[30_000, 1]  # a repeat in row 30000 (unsorted, or sorted then broken)
+        s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
+        assert s == asaga.EINVAL and "repeated column in row 30000" in err, err
+        bad = c.copy()
+        bad[40_000, 2] = d  # out of range in the middle of a row
+        s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
+        assert s == asaga.EINVAL and str(40_000 * k + 2) in err, err
