@@ -232,17 +232,23 @@ def update_hbm_bytes(p, storage, info=None):
 
 # ---------------------------------------------------------------- reference arm
 
-def time_checker(p, seconds, steps=None, warmup=0):
-    """Float64 CPU checker: one step = one epoch of serial Sparse SAGA + the
-    float64 objective.  Runs `steps` steps, or as many as fit in `seconds`."""
+REFERENCE_STEPS_PER_EPOCH = 16
+
+def time_checker(p, seconds, steps=None, warmup=0, per_epoch=1):
+    """Float64 CPU checker.  One step = n/per_epoch serial Sparse SAGA updates,
+    with the float64 objective after every per_epoch-th step (per_epoch = 1:
+    a step is one epoch and its objective).  Runs `steps` steps, or as many as
+    fit in `seconds`; returns (epochs/s, steps done, seconds)."""
     from oracle import reference as R
     L = R.lipschitz(p)
     gamma, D = 1.0 / (3.0 * L), R.reweighting(p)
     st = R.State.zeros(p)
+    count = -(-p.n // per_epoch)
 
     def step(k):
-        R.sparse_saga(p, st, synth.sample_indices(p.n, p.n, 30, k + 1), gamma, D)
-        return R.objective(p, st.x)
+        R.sparse_saga(p, st, synth.sample_indices(p.n, count, 30, k + 1), gamma, D)
+        if (k + 1) % per_epoch == 0:
+            R.objective(p, st.x)
 
     for k in range(warmup):
         step(k)
@@ -253,7 +259,7 @@ def time_checker(p, seconds, steps=None, warmup=0):
         el = time.perf_counter() - t0
         if (steps is not None and done >= steps) or (steps is None and el >= seconds):
             break
-    return done / el, done, el
+    return done * count / p.n / el, done, el
 
 
 def time_cpu_asaga(p, seconds, fstar, target):
@@ -288,14 +294,18 @@ def run_reference(args, p, wl):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    eps, done, el = time_checker(p, args.cpu_seconds, steps=args.steps, warmup=min(args.warmup, 1))
+    # each step is a bounded sample: 1/16 of an epoch of serial updates, the
+    # objective after every 16th step, so K steps stay within minutes
+    per_epoch = REFERENCE_STEPS_PER_EPOCH
+    eps, done, el = time_checker(p, args.cpu_seconds, steps=args.steps, warmup=args.warmup, per_epoch=per_epoch)
     line = {
         "impl": "reference", "metric": "epochs/s", "value": eps, "unit": "epochs/s", "n_gpus": args.gpus,
-        "steps": done, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / done, "higher_is_better": True,
+        "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["desc"]},
         "cpu_baseline": {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0"},
+                         "sample": f"{done} steps of n/{per_epoch} serial float64 Sparse SAGA updates, the "
+                                   f"float64 objective after every {per_epoch}th, from x=0 ({done / per_epoch:.2f} epochs)"},
         "e2e": {"value": eps, "unit": "epochs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
