@@ -58,8 +58,9 @@ WORKLOADS = {
 }
 ABAR_EVERY = 5
 TARGET = 1e-6
-# 256 independent l2-logistic instances (a regularisation path): BASELINE's batch configuration with n and d
-# scaled by 1/10 so that the seeded CPU generator and the float64 certificates stay within minutes
+# 256 independent l2-logistic instances (a regularisation path): the batch workload (n ~ U[10k, 200k],
+# d ~ U[1k, 50k]) with n and d scaled by 1/10 so that the seeded CPU generator and the float64
+# certificates stay within minutes
 BATCH = dict(count=256, seed=51, n_range=(1_000, 20_000), d_range=(100, 5_000), density_range=(0.005, 0.02),
              lam_range=(1e-6, 1e-2), storage="bf16")
 BATCH_DESC = ("256 l2-logistic instances: n~U[1000,20000], d~U[100,5000], density~U[0.5%,2%], Zipf(1.1) columns, "
