@@ -249,8 +249,9 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     tolerance, one with more warps must be 1.2x faster.  If no candidate
  *     settles, the race is run again one notch further inside (twice at
  *     most);
- *  3. smaller steps at the winning warp count while they score better, then
- *     a confirmation trial of twice the length that must still show a
+ *  3. smaller steps at the winning warp count while they score better (if
+ *     none does, one notch larger, kept if it scores better), then a
+ *     confirmation trial of twice the length that must still show a
  *     downward trend (else one notch smaller a step, three times at most);
  *  4. the update kernel's block shape at the winner: eight warps per block
  *     or the warps spread evenly over the SMs, whichever epoch is faster.

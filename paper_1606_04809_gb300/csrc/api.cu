@@ -1170,11 +1170,19 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     }
     // 3. at the winning warp count, smaller steps while they are faster (well
     //    conditioned problems need no more than a small step per update)
+    const int k_raced = best_k;
     if (std::isfinite(best_ms))
         for (int k = best_k + 1; k <= kBottom; ++k) {
             TRY(candidate(best_w, k, &improved));
             if (!improved) break;
         }
+    //    When none was, one notch larger: the race put every warp count one
+    //    notch inside the frontier measured at the probe count, and fewer
+    //    warps can carry a larger W x gamma than that (measured: URL-shaped
+    //    at 256 warps reaches 1e-6 in 14 epochs one notch out, 19 at the raced
+    //    step).  The confirmation below still guards against a late plateau.
+    if (std::isfinite(best_ms) && best_k == k_raced && best_k - 1 >= kTop)
+        TRY(candidate(best_w, best_k - 1, &improved));
     // confirmation: the winner over a trial twice as long must still show a
     // downward trend (a plateau can set in after a short trial's early
     // progress); one notch smaller a step while it does not (three times at most)
