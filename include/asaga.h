@@ -250,7 +250,8 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     settles, the race is run again one notch further inside (twice at
  *     most);
  *  3. smaller steps at the winning warp count while they score better (if
- *     none does, one notch larger, kept if it scores better), then a
+ *     none does and the warps are at most n/256, one notch larger, kept if
+ *     it scores better), then a
  *     confirmation trial of twice the length that must still show a
  *     downward trend (else one notch smaller a step, three times at most);
  *  4. the update kernel's block shape at the winner: eight warps per block

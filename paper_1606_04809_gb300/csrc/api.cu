@@ -1180,8 +1180,11 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     //    notch inside the frontier measured at the probe count, and fewer
     //    warps can carry a larger W x gamma than that (measured: URL-shaped
     //    at 256 warps reaches 1e-6 in 14 epochs one notch out, 19 at the raced
-    //    step).  The confirmation below still guards against a late plateau.
-    if (std::isfinite(best_ms) && best_k == k_raced && best_k - 1 >= kTop)
+    //    step).  Only where the overlap stays far below n (W <= n/256, tau
+    //    below n/64): on small problems the larger step was seen to pass the
+    //    trials and then stall on a plateau.  The confirmation below still
+    //    guards against a late plateau.
+    if (std::isfinite(best_ms) && best_k == k_raced && best_k - 1 >= kTop && (int64_t)best_w * 256 <= c->n)
         TRY(candidate(best_w, best_k - 1, &improved));
     // confirmation: the winner over a trial twice as long must still show a
     // downward trend (a plateau can set in after a short trial's early
