@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <system_error>
 #include <thread>
 #include <vector>
 
@@ -241,7 +242,11 @@ bool parallel_check(int64_t count, int64_t min_chunk, int max_threads, F body, s
         th.reserve(nt);
         for (int t = 0; t < nt; ++t) {
             const int64_t lo = count * t / nt, hi = count * (t + 1) / nt;
-            th.emplace_back([&, t, lo, hi] { body(lo, hi, &errs[t]); });
+            try {
+                th.emplace_back([&, t, lo, hi] { body(lo, hi, &errs[t]); });
+            } catch (const std::system_error &) {  // no more threads: this block on the caller's
+                body(lo, hi, &errs[t]);
+            }
         }
         for (auto &x : th) x.join();
     }
@@ -664,7 +669,11 @@ struct ContentCheck {
     std::string msg;
     int64_t max_row_len = 0;
     void start(const asaga_problem *p, const asaga_options *o) {
-        th = std::thread([this, p, o] { status = validate_content(p, o, &max_row_len, &msg); });
+        try {
+            th = std::thread([this, p, o] { status = validate_content(p, o, &max_row_len, &msg); });
+        } catch (const std::system_error &) {  // no thread to be had: check on this one
+            status = validate_content(p, o, &max_row_len, &msg);
+        }
     }
     void join() {
         if (th.joinable()) th.join();
