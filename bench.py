@@ -169,11 +169,12 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def ncu_summary(workload):
+def ncu_summary(workload, profile=None):
     """Per-launch DRAM bytes and the L2 throughput (% of peak) of the update
-    kernel from the committed ncu summary, if it was taken on the current
-    kernel source; None otherwise."""
-    path = os.path.join(ROOT, "profiles", f"update_kernel_{workload}.md")
+    kernel from the committed ncu summary (profiles/update_kernel_<workload>.md,
+    or profiles/<profile>.md), if it was taken on the current kernel source;
+    None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"{profile or 'update_kernel_' + workload}.md")
     src = os.path.join(ROOT, "paper_1606_04809_gb300", "csrc", "update.cu")
     if not os.path.exists(path):
         return None
@@ -357,16 +358,39 @@ def run_batch(args):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    launches = 0
+    launches, seg_s = 0, 0.0
     for _ in range(args.steps):
         st, res = asaga.asaga_batch_run(b.b, b.count, 1)
         launches += res[0].kernel_launches
+        seg_s += res[0].solver_seconds  # the batch epoch's segment (one CUDA graph)
     e1.record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
     b.close()
+    # HBM roofline of the batch epoch: A's bytes and the per-update row data of
+    # every instance over the segment's device time (update launch plus the
+    # batched objective, which the segment also holds: a lower bound on the
+    # update kernel's own rate)
+    hbm_bytes = sum(update_hbm_bytes(p, "bf16") for p in ps)
+    peak, peak_kind = measured_peak_hbm()
+    seg_ms = 1e3 * seg_s / args.steps
+    achieved = hbm_bytes / (seg_ms * 1e-3) / 1e9
+    ncu = ncu_summary("batch256", profile="batch_update_kernel_batch256") or {}
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu.get("traffic"),
+                "kernel": "batch segment: batch_update_kernel + the batched objective (one CUDA graph per batch epoch)",
+                "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": seg_ms, "peak_source": peak_kind,
+                "l2_throughput_pct_of_peak_ncu": ncu.get("l2_pct"), "dram_throughput_pct_of_peak_ncu": ncu.get("dram_pct")}
     # time to 1e-6 for every instance of the batch
     b = asaga.Batch(ps, storage="bf16", values_dtype="bf16", epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
                     cuda_stream=stream.cuda_stream)
@@ -408,6 +432,19 @@ def run_batch(args):
                   "batch_seconds_for_same_instances": batch_sample,
                   "batch_seconds_all_instances": batch_dev,
                   "speedup_batch_vs_single_same_instances": tot_dev / batch_sample if batch_sample > 0 else None}
+    # CPU baseline: the float64 oracle, three epochs (each with its objective)
+    # on every 4th instance, scaled to the whole batch by nonzeros
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        sample = list(range(0, len(ps), 4))
+        epochs_each, el = 3, 0.0
+        for i in sample:
+            el += time_checker(ps[i], 0.0, steps=epochs_each)[2]
+        nnz_sample = sum(ps[i].nnz for i in sample)
+        per_batch = el / epochs_each * sum(p.nnz for p in ps) / max(1, nnz_sample)
+        cpu = {"value": 1.0 / per_batch, "unit": "epochs/s (whole batch)", "cores": 1, "kind": "oracle",
+               "sample": f"{epochs_each} epochs of serial float64 Sparse SAGA + objective on {len(sample)} of "
+                         f"{len(ps)} instances ({el:.2f} s), scaled to the batch by nonzeros"}
     if rank == 0:
         line = {"metric": "epochs/s", "value": world * args.steps / (ms * 1e-3), "unit": "epochs/s (whole batch)",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -416,7 +453,7 @@ def run_batch(args):
                                                 "nnz_total": int(sum(p.nnz for p in ps_all))},
                 "instance_epochs_per_s": world * args.steps * len(ps) / (ms * 1e-3),
                 "time_to_target": ttt, "autotune_wall_seconds": tune_s, "one_at_a_time_fp32": single,
-                "gpu_launches": launches}
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
