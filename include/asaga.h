@@ -98,7 +98,9 @@ typedef struct {
  *   seed                 seed of the row sampler (counter-based SplitMix64).
  *   epochs_per_segment   epochs between float64 objective evaluations.
  *   abar_recompute_every segments between float64 recomputations of abar
- *                        from the memory (0 = never).
+ *                        from the memory (0 = never), counted over the
+ *                        context's life across asaga_run calls (restarted
+ *                        by asaga_set_state and asaga_autotune).
  *   timeout_s            wall-clock limit of one asaga_run (0 = none).
  *   cuda_stream          cudaStream_t to run on; NULL = a stream the library
  *                        creates.  All work of a context is ordered on it.

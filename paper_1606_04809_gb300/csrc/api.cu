@@ -46,6 +46,7 @@ struct asaga_ctx {
     int abar_every = 0;
     double timeout_s = 0;
     int64_t updates_done = 0;
+    int64_t segments_done = 0;  // over the context's life: the abar recomputation cadence
     int eval_grid = 1;
     int64_t launches = 0;
     int64_t device_bytes = 0;
@@ -90,6 +91,7 @@ struct asaga_batch {
     bool dense = false;
     int epochs_per_segment = 1;
     int abar_every = 0;
+    int64_t segments_done = 0;  // over the batch's life: the abar recomputation cadence
     int resident_blocks = 1;
     std::vector<int> warps;        // per instance, a multiple of 4 (one block = 4 warps)
     std::vector<int> block_begin;  // first block of each instance
@@ -844,7 +846,9 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
         if (count > 0) TRY(launch_updates(c, u, err));
         CK(cudaEventRecord(c->ev[1], c->stream), "event");
         ++seg;
-        if (c->abar_every > 0 && seg % c->abar_every == 0) TRY(enqueue_recompute(c, err));
+        // every abar_every-th segment of the context, counted across calls
+        const bool recompute = c->abar_every > 0 && ++c->segments_done % c->abar_every == 0;
+        if (recompute) TRY(enqueue_recompute(c, err));
         TRY(enqueue_objective(c, err));
         CK(cudaEventRecord(c->ev[2], c->stream), "event");
         CK(cudaMemcpyAsync(c->hout, c->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy f");
@@ -860,7 +864,7 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
         epochs_done += ep;
         r.segments = seg;
         r.f_last = c->hout[0];
-        if (c->abar_every > 0 && seg % c->abar_every == 0) r.abar_drift = c->hout[1];
+        if (recompute) r.abar_drift = c->hout[1];
         if (target > 0 || std::isfinite(f_star)) r.rel_subopt = (r.f_last - f_star) / std::fabs(f_star);
         if (*c->hstatus & 4) {
             st = ASAGA_ECUDA;
@@ -908,6 +912,7 @@ asaga_status reset_state(asaga_ctx *c, std::string *err) {
     CK(cudaMemset2DAsync(c->state, (size_t)c->stride * sizeof(float4), 0, 2 * sizeof(float), c->d, c->stream),
        "memset state");
     c->updates_done = 0;
+    c->segments_done = 0;
     return ASAGA_OK;
 }
 
@@ -1602,7 +1607,7 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
                 --n_active;
             }
         }
-        if (b->abar_every > 0 && seg % b->abar_every == 0) {
+        if (b->abar_every > 0 && ++b->segments_done % b->abar_every == 0) {  // counted across calls
             for (int i = 0; i < b->count; ++i)
                 if (active[i]) TRY(enqueue_recompute(b->ctx[i], err));
             TRY(stream_sync(b->ctx[0], err));
@@ -1843,6 +1848,7 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
     }
     const std::vector<int> &kc = second ? kc2 : kc1;
     const std::vector<double> &pc = second ? pc2 : pc1;
+    b->segments_done = 0;  // the tuned state starts at x = 0: the abar cadence restarts
     for (int i = 0; i < N; ++i) {
         asaga_ctx *c = b->ctx[i];
         if (kc[i] != -1000) c->gamma = c->gamma_base * std::pow(2.0, -0.5 * kc[i]);
@@ -2028,6 +2034,7 @@ asaga_status asaga_set_state(asaga_ctx *c, const float *x, const float *abar, co
     if (alpha) CK(cudaMemcpyAsync(c->alpha, alpha, c->n * sizeof(float), cudaMemcpyHostToDevice, c->stream), "copy alpha");
     TRY(stream_sync(c, err));
     c->updates_done = updates_done;
+    c->segments_done = 0;  // the abar recomputation cadence restarts with the restored state
     return ASAGA_OK;
 }
 

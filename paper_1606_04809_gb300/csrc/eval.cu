@@ -212,6 +212,48 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_rows_kernel(const EvalPara
     }
 }
 
+// The abar recomputation: acc[v] += sum_i (alpha_i/n) a_iv.  A row's weight
+// is one load, so a warp takes a row and its lanes split the entries
+// (coalesced loads of the CSR streams, unlike one thread per row, which
+// mode 0 needs for its float64 phi'); the frequent columns (kSlotsMode 2) or
+// all d dense columns (kSlotsMode 1) accumulate per block in shared memory
+// as in scatter_rows_kernel.  Rows with alpha_i = 0 add nothing and are
+// skipped.
+template <typename T, typename I, bool kDense, int kSlotsMode>
+__global__ void __launch_bounds__(kEvalBlock) scatter_alpha_rows_kernel(const EvalParams P, double *acc) {
+    extern __shared__ double sacc[];
+    const double inv_n = 1.0 / (double)P.n;
+    const int nslots = kSlotsMode == 1 ? (int)P.d : (kSlotsMode == 2 ? P.n_hot : 0);
+    if (kSlotsMode) {
+        for (int v = threadIdx.x; v < nslots; v += blockDim.x) sacc[v] = 0.0;
+        __syncthreads();
+    }
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < P.n; i += nwarps) {
+        const double w = (double)__ldg(P.alpha + i) * inv_n;  // the same in every lane
+        if (w == 0.0) continue;
+        int64_t start;
+        int len;
+        row_range<T, kDense>(P, i, start, len);
+        for (int k = lane; k < len; k += 32) {
+            const int c = kDense ? k : col_stream<I>(P.col_idx, start + k);
+            const double contrib = w * (double)value_at<T>(P.values, i, start + k);
+            const int slot = kSlotsMode == 1 ? c : (kSlotsMode == 2 ? __ldg(P.hot_slot + c) : -1);
+            if (slot >= 0)
+                atomicAdd(sacc + slot, contrib);
+            else
+                atomicAdd(acc + c, contrib);
+        }
+    }
+    if (kSlotsMode) {
+        __syncthreads();
+        for (int v = threadIdx.x; v < nslots; v += blockDim.x)
+            atomicAdd(acc + (kSlotsMode == 1 ? v : P.hot_col[v]), sacc[v]);
+    }
+}
+
 __global__ void __launch_bounds__(kEvalBlock) column_finish_kernel(const EvalParams P, int mode, double *acc,
                                                                    double *partial) {
     double local = 0.0;
@@ -410,6 +452,21 @@ struct ScatterRows {
     double *acc;
     cudaStream_t s;
     template <typename T, typename I, bool kDense> cudaError_t run() const {
+        if (mode == 1) {  // abar from alpha: a warp per row
+            if constexpr (kDense) {
+                if (p.d <= kSmemCols)
+                    scatter_alpha_rows_kernel<T, I, true, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, acc);
+                else
+                    scatter_alpha_rows_kernel<T, I, true, 0><<<grid, kEvalBlock, 0, s>>>(p, acc);
+            } else {
+                if (p.n_hot > 0 && p.hot_slot)
+                    scatter_alpha_rows_kernel<T, I, false, 2>
+                        <<<grid, kEvalBlock, (size_t)p.n_hot * sizeof(double), s>>>(p, acc);
+                else
+                    scatter_alpha_rows_kernel<T, I, false, 0><<<grid, kEvalBlock, 0, s>>>(p, acc);
+            }
+            return cudaGetLastError();
+        }
         if (kDense && p.d <= kSmemCols) {
             scatter_rows_kernel<T, I, kDense, 1><<<grid, kEvalBlock, (size_t)p.d * sizeof(double), s>>>(p, mode, acc);
         } else if (!kDense && p.n_hot > 0 && p.hot_slot) {

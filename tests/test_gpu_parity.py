@@ -388,3 +388,18 @@ def test_plain_writes_break_the_average_invariant():
             drift[plain] = asaga.asaga_recompute_abar(c.ctx)
     assert drift[0] < 1e-5
     assert drift[1] > 30 * drift[0]
+
+
+def test_abar_recompute_cadence_counts_across_calls():
+    """abar_recompute_every counts segments over the context's life, so a loop of
+    one-epoch asaga_run calls recomputes abar every k-th call (and reports its
+    drift then), not never; asaga_set_state restarts the count."""
+    p = synth.rcv1_like(seed=23, n=20000, d=3000)
+    with asaga.Context(p, storage="f32", seed=3, max_warps=128, gamma=0.1, abar_recompute_every=2) as c:
+        drifts = [asaga.asaga_run(c.ctx, 1)[1].abar_drift for _ in range(5)]
+        assert drifts[0] == 0.0 and drifts[2] == 0.0 and drifts[4] == 0.0, drifts
+        assert drifts[1] > 0.0 and drifts[3] > 0.0, drifts  # float32 running sums drift after an epoch
+        x, abar, alpha = asaga.asaga_get_state(c.ctx)
+        asaga.asaga_set_state(c.ctx, x, abar, alpha, 5 * p.n)
+        after = [asaga.asaga_run(c.ctx, 1)[1].abar_drift for _ in range(2)]
+        assert after[0] == 0.0 and after[1] > 0.0, after
