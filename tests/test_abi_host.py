@@ -174,10 +174,12 @@ def test_line_probe_arguments_are_checked_before_any_cuda_call(lib):
     assert L.asaga_probe_line_rate(4, 10, None) == asaga.EINVAL
 
 
-def test_rows_in_any_column_order_are_checked_alike(lib):
+# a stamp array per thread (d <= 2^18); a per-row hash set beyond, with short rows and with long
+# ones that outgrow its first 64 slots
+@pytest.mark.parametrize("n,d,k", [(50_000, 3000, 6), (50_000, 400_000, 6), (2_000, 400_000, 300)])
+def test_rows_in_any_column_order_are_checked_alike(lib, n, d, k):
     """Increasing rows take a fast path; other rows the general check, with the same verdicts."""
     g = np.random.default_rng(1)
-    n, d, k = 50_000, 3000, 6
     col = np.stack([g.choice(d, k, replace=False) for _ in range(n)]).astype(np.int32)  # unsorted, distinct
     row_ptr = np.arange(n + 1, dtype=np.int64) * k
     vals = np.ones(n * k)
@@ -185,12 +187,13 @@ def test_rows_in_any_column_order_are_checked_alike(lib):
     assert create(row_ptr, col.ravel(), vals, y, n=n, d=d)[0] != asaga.EINVAL
     srt = np.sort(col, axis=1)
     assert create(row_ptr, srt.ravel(), vals, y, n=n, d=d)[0] != asaga.EINVAL
+    r1, r2 = 3 * n // 5, 4 * n // 5
     for c in (col, srt):
         bad = c.copy()
-        bad[30_000, 4] = bad[30_000, 1]  # a repeat in row 30000 (unsorted, or sorted then broken)
+        bad[r1, k - 2] = bad[r1, 1]  # a repeat (unsorted, or sorted then broken), far apart in long rows
         s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
-        assert s == asaga.EINVAL and "repeated column in row 30000" in err, err
+        assert s == asaga.EINVAL and f"repeated column in row {r1}" in err, err
         bad = c.copy()
-        bad[40_000, 2] = d  # out of range in the middle of a row
+        bad[r2, 2] = d  # out of range in the middle of a row
         s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
-        assert s == asaga.EINVAL and str(40_000 * k + 2) in err, err
+        assert s == asaga.EINVAL and str(r2 * k + 2) in err, err
