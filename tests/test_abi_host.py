@@ -197,3 +197,14 @@ def test_rows_in_any_column_order_are_checked_alike(lib, n, d, k):
         bad[r2, 2] = d  # out of range in the middle of a row
         s, err = create(row_ptr, bad.ravel(), vals, y, n=n, d=d)
         assert s == asaga.EINVAL and str(r2 * k + 2) in err, err
+
+
+@pytest.mark.parametrize("gamma", [0.0, -1.0])
+def test_a_step_of_zero_or_below_selects_the_default(lib, gamma):
+    """options.gamma <= 0 means 1/(3L) (include/asaga.h), so it is not an input
+    error: without a GPU the call gets past the checks to the CUDA error."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s, err = create(*small_csr(), gamma=gamma)
+    assert s == asaga.ECUDA, err
