@@ -478,7 +478,10 @@ void asaga_batch_destroy(asaga_batch *b);
  * that overlap on the GPU -- on different streams or from different host
  * threads -- race and corrupt each other's results; order them.  The first
  * call on a device looks the scratch address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current; make that first call before any stream capture.  The
+ * address belongs to the device's CUDA context: after a cudaDeviceReset the
+ * next call on that device finds a new context and looks the address up
+ * again, so that call too should come before any stream capture.
  * EINVAL: n < 1, d outside [1, ASAGA_NOALLOC_MAX_D], a NULL array; ECUDA: a
  * CUDA call failed.  asaga_last_error(NULL) gives the reason.
  */

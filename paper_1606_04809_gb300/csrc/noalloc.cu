@@ -14,7 +14,12 @@
 // The scratch is a file-scope __device__ array.  In host code its name only
 // stands for the symbol, not for a device address, so the first call on each
 // device (with that device current) looks the address up once with
-// cudaGetSymbolAddress and passes that pointer to the kernels.
+// cudaGetSymbolAddress and passes that pointer to the kernels.  The address
+// belongs to the device's CUDA context: a cudaDeviceReset destroys that
+// context (and the array with it), so the cached address is keyed by the
+// context's process-unique id (cuCtxGetId) and looked up again when the
+// current context is a different one.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,11 +43,39 @@ __device__ __align__(256) double g_noalloc_partial[kNoAllocBlocks];
 struct Scratch {
     double *acc = nullptr;
     double *partial = nullptr;
+    unsigned long long ctx_id = 0;  // context the addresses belong to (0: none yet)
 };
 Scratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mutex;
 
-// Device addresses of the scratch on the current device (looked up once per device).
+// Process-unique id of the calling thread's current CUDA context, 0 when
+// there is none yet (or the driver cannot say).  The two driver calls are
+// fetched through the runtime, so the library does not link libcuda itself.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device addresses of the scratch on the current device: the set-up, once
+// per device and context (again after a cudaDeviceReset made a new context).
 cudaError_t scratch_for_current_device(Scratch *out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -50,7 +83,8 @@ cudaError_t scratch_for_current_device(Scratch *out) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
     Scratch &s = g_scratch[dev];
-    if (!s.acc || !s.partial) {
+    const unsigned long long id = current_context_id();
+    if (!s.acc || !s.partial || id == 0 || id != s.ctx_id) {
         void *acc = nullptr, *partial = nullptr;
         e = cudaGetSymbolAddress(&acc, g_noalloc_acc);
         if (e != cudaSuccess) return e;
@@ -58,6 +92,7 @@ cudaError_t scratch_for_current_device(Scratch *out) {
         if (e != cudaSuccess) return e;
         s.acc = static_cast<double *>(acc);
         s.partial = static_cast<double *>(partial);
+        s.ctx_id = current_context_id();  // the lookup made the device's context current
     }
     *out = s;
     return cudaSuccess;

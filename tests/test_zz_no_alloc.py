@@ -4,13 +4,20 @@ It serves callers that cannot allocate device memory: processes with a
 fixed device-memory footprint reserved up front, code inside a framework
 that owns every device allocation, and paths that cannot afford cudaFree's
 device-wide synchronisation.  It must give the same result as the context's
-asaga_recompute_abar, call after call, with its scratch living in a fixed
-array of the library instead of allocated memory.  This file is collected
-last on purpose.
+asaga_recompute_abar and as the float64 CPU checker's abar = (1/n) sum_i
+alpha_i a_i, call after call, with its scratch living in a fixed array of the
+library instead of allocated memory.  This file is collected last on purpose.
+
+Tolerance against the checker: both sides sum the same float64 products
+(float32 alpha_i and a_iv widened exactly) in different orders and the
+library rounds the sum to float32, so each column differs from the checker's
+float64 value by at most half a float32 ulp (2^-24 relative) plus float64
+reordering error (~1e-15 relative): rtol 2^-23 covers it with a factor two.
 """
 import numpy as np
 import pytest
 
+from oracle import reference as R
 from paper_1606_04809_gb300 import asaga, build, synth
 
 
@@ -39,6 +46,8 @@ def test_matches_the_context_recompute_on_two_calls_in_a_row(lib):
         _, abar_before, alpha = asaga.asaga_get_state(c.ctx)
         drift_ref = asaga.asaga_recompute_abar(c.ctx)  # the existing entry point
         abar_ref = asaga.asaga_get_state(c.ctx)[1]
+    abar_exact = R.abar_from_scratch(p, alpha.astype(np.float64))  # the float64 checker
+    drift_exact = float(np.max(np.abs(abar_before.astype(np.float64) - abar_exact)))
 
     dev = torch.device("cuda", 0)
     row_ptr = torch.from_numpy(np.ascontiguousarray(p.row_ptr, dtype=np.int64)).to(dev)
@@ -55,4 +64,6 @@ def test_matches_the_context_recompute_on_two_calls_in_a_row(lib):
         got = abar_d.cpu().numpy()
         # both sum in float64 (atomics in different orders) and round to float32
         np.testing.assert_allclose(got, abar_ref, rtol=2.5e-7, atol=1e-12, err_msg=f"call {call}")
+        np.testing.assert_allclose(got, abar_exact, rtol=2.0 ** -23, atol=1e-30, err_msg=f"call {call} vs checker")
         assert drift_d.item() == pytest.approx(drift_ref, rel=1e-6, abs=1e-12)
+        assert drift_d.item() == pytest.approx(drift_exact, rel=1e-9, abs=1e-15)
