@@ -90,7 +90,7 @@ typedef struct {
  *                        and reweighted by D_i, Sec. 4.2).
  *   storage_dtype        device type of A's values: F32, BF16 or F16 (the
  *                        iterate, memory and dot products are always F32).
- *   max_warps            concurrent solver warps ("cores"); 0 = automatic
+ *   max_warps            concurrent solver warps; 0 = automatic
  *                        (a bound derived from n keeps the overlap well below
  *                        n/10, the condition of Theorem 2).
  *   deterministic        1 = one warp processes the updates strictly in
@@ -175,6 +175,9 @@ typedef struct {
                             autotuner found the warps faster spread over the SMs */
     int col_index_bytes; /* 4, 2 (compact uint16 indices) or 0 (dense)          */
     int row_values;      /* 1 when A is held as one value per row (compact)     */
+    int64_t row_threshold; /* rows longer than this take the multi-warp row path
+                              (0: every row; -1: none; see asaga_set_row_path)  */
+    int row_group;       /* warps per core of the multi-warp row path (1: none)  */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */
@@ -184,6 +187,8 @@ typedef struct {
     double score;        /* higher is better; -1 when no trial settled          */
     int trials;          /* (warps, gamma) pairs tried                          */
     double seconds;      /* device time spent in the trials                      */
+    int64_t row_threshold; /* chosen row path (asaga_set_row_path): threshold... */
+    int row_group;       /* ...and warps per multi-warp core                     */
 } asaga_tune_result;
 
 /* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
@@ -257,7 +262,14 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     confirmation trial of twice the length that must still show a
  *     downward trend (else one notch smaller a step, three times at most);
  *  4. the update kernel's block shape at the winner: eight warps per block
- *     or the warps spread evenly over the SMs, whichever epoch is faster.
+ *     or the warps spread evenly over the SMs, whichever epoch is faster;
+ *  5. the row path at the winner (the same warps and step, regrouped into
+ *     cores; see asaga_set_row_path): multi-warp cores of G = 2, 4, 8 warps
+ *     for every row (when the mean row has at least 32 G entries) or for the
+ *     rows longer than T = 128, 256, 512 entries (when they hold at least 2%
+ *     of the nonzeros), each timed over two epochs after one untimed; the
+ *     two fastest that beat single warps by 3% run a race trial in turn,
+ *     and the first whose predicted time beats the winner's by 3% is kept.
  * If no trial converges, the defaults stay.  score = 1 / (predicted
  * seconds of the winner), -1 when none settled.  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
@@ -365,6 +377,35 @@ asaga_status asaga_get_info(asaga_ctx *ctx, asaga_info *info);
  * in deterministic mode (one warp). */
 asaga_status asaga_set_schedule(asaga_ctx *ctx, int warps, double gamma, int warps_per_block);
 
+/* The multi-warp row path (Algorithm 2's update of one row spread over the
+ * warps of a block).  Every concurrent update runs on a "core": a single
+ * warp, except that rows with more than `threshold` entries are updated by
+ * cores of `group` warps of one block: lane l of warp w owns the row's
+ * entries 32 (q group + w) + l,
+ * q = 0, 1, ...; the warps add their partial dot products a_i . x^ in shared
+ * memory behind a named barrier and scatter their own entries with the same
+ * delta.  A core of g warps holds 256 g entries of a row in registers (128 g
+ * for dense rows); every entry's state is still read once per update, the
+ * entries past that in a per-core scratch array the library allocates.
+ *   threshold  -1: no row takes the multi-warp path (the default); 0: every
+ *              row; T > 0: rows longer than T entries, the others on
+ *              single-warp cores.
+ * The path regroups the warps of the schedule (asaga_set_schedule; with
+ * T > 0 the long rows' cores get the share of the warps that those rows
+ * hold of the nonzeros) and keeps their number: measured on a GB300, the
+ * stability frontier lies at a product of total warps and step, not of
+ * concurrent updates, so a step that converges on W single warps also does
+ * on W warps grouped by 4.
+ *              Each path's cores take the launch's updates t = core,
+ *              core + cores, ... whose rows belong to that path, so every
+ *              sampled update is applied exactly once (Algorithm 2's row
+ *              sequence is unchanged; only its assignment to cores is).
+ *   group      warps per multi-warp core: 1, 2, 4 or 8 (1 = none).
+ * In deterministic mode (one core, strictly in order) only threshold -1 or
+ * 0 applies: threshold 0 replays the updates on one core of `group` warps.
+ * EINVAL on other values.  asaga_autotune chooses this too (its step 5). */
+asaga_status asaga_set_row_path(asaga_ctx *ctx, int64_t threshold, int group);
+
 /* Reason for the last failure of a call on ctx (or, when ctx is NULL, of
  * the calling thread's last asaga_create, asaga_sample_rows,
  * asaga_probe_line_rate or asaga_recompute_abar_noalloc); never NULL. */
@@ -402,10 +443,15 @@ asaga_status asaga_batch_create(asaga_batch **out, int count, const asaga_proble
  * or max_epochs epochs have run.  results[i] (may be NULL) holds instance
  * i's epochs, updates, f_last and rel_subopt; its solver_seconds is the
  * device time of the shared segments up to the one after which it stopped,
- * i.e. its time to target inside the batch.  f_star may be NULL when
- * target <= 0.  OK when every instance reached the target (or target <= 0),
- * ENOTCONVERGED otherwise, EDIVERGED if an objective turned non-finite,
- * ECANCELLED after asaga_batch_cancel. */
+ * i.e. its time to target inside the batch: every segment's update
+ * launch, batched float64 objective and (every
+ * options[0].abar_recompute_every-th segment, counted over the batch's life)
+ * batched float64 abar recomputation, all captured in the segment's CUDA
+ * graph; abar_drift is the drift that instance's last recomputation found.
+ * f_star may be NULL when target <= 0.  OK when every instance reached the
+ * target (or target <= 0), ENOTCONVERGED otherwise, EDIVERGED if an
+ * objective turned non-finite, ECANCELLED after asaga_batch_cancel, ECUDA if
+ * the update kernel reported a malformed row range or a staging failure. */
 asaga_status asaga_batch_run(asaga_batch *b, double max_epochs, double target, const double *f_star,
                              asaga_result *results);
 
@@ -437,6 +483,19 @@ asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tun
  * gamma[i]; either array may be NULL.  EINVAL if the warps cannot all be
  * resident at once. */
 asaga_status asaga_batch_set_schedule(asaga_batch *b, const int *warps, const double *gamma);
+
+/* Per-instance row paths (see asaga_set_row_path): threshold[i] >= -1 and
+ * group[i] in {1, 2, 4} (a block of the batch kernel has 4 warps).  An
+ * instance's blocks then hold 4 single-warp cores or 4/group multi-warp
+ * cores; with both paths in use (threshold[i] > 0) its blocks are split in
+ * proportion to the share of its nonzeros in the long rows.  EINVAL on
+ * NULL arrays or other values. */
+asaga_status asaga_batch_set_row_paths(asaga_batch *b, const int64_t *threshold, const int *group);
+
+/* Every instance back to x = 0, alpha = 0, abar = 0 and sampler position 0,
+ * keeping the schedule (warps, steps, row paths); the abar recomputation
+ * cadence restarts.  EINVAL: b NULL. */
+asaga_status asaga_batch_reset(asaga_batch *b);
 
 /* As asaga_get_state / asaga_get_info for instance i. */
 asaga_status asaga_batch_get_state(asaga_batch *b, int i, float *x, float *abar, float *alpha);

@@ -67,7 +67,8 @@ class asaga_info(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("delta", ctypes.c_double), ("warps", ctypes.c_int),
                 ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("warps_per_block", ctypes.c_int),
-                ("col_index_bytes", ctypes.c_int), ("row_values", ctypes.c_int)]
+                ("col_index_bytes", ctypes.c_int), ("row_values", ctypes.c_int),
+                ("row_threshold", ctypes.c_int64), ("row_group", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,7 +76,8 @@ class asaga_info(ctypes.Structure):
 
 class asaga_tune_result(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int), ("gamma", ctypes.c_double), ("score", ctypes.c_double),
-                ("trials", ctypes.c_int), ("seconds", ctypes.c_double)]
+                ("trials", ctypes.c_int), ("seconds", ctypes.c_double), ("row_threshold", ctypes.c_int64),
+                ("row_group", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -137,6 +139,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_cancel.restype = i32
     L.asaga_set_schedule.argtypes = [vp, i32, dbl, i32]
     L.asaga_set_schedule.restype = i32
+    L.asaga_set_row_path.argtypes = [vp, i64, i32]
+    L.asaga_set_row_path.restype = i32
+    L.asaga_batch_set_row_paths.argtypes = [vp, vp, vp]
+    L.asaga_batch_set_row_paths.restype = i32
+    L.asaga_batch_reset.argtypes = [vp]
+    L.asaga_batch_reset.restype = i32
     L.asaga_batch_cancel.argtypes = [vp]
     L.asaga_batch_cancel.restype = i32
     L.asaga_destroy.argtypes = [vp]
@@ -218,7 +226,11 @@ def host_problem(p, values_dtype: str = "f64") -> Problem:
     """asaga_problem over the host arrays of a generated problem (values sent
     as float64 by default; the library rounds them to the storage type)."""
     np_dt = {"f64": np.float64, "f32": np.float32, "f16": np.float16}
-    if values_dtype == "bf16":  # values already on the bf16 grid: keep the top 16 bits
+    if values_dtype == "bf16" and p.values.dtype == np.uint16:  # raw bfloat16 bits already
+        vals = np.ascontiguousarray(p.values)
+    elif p.values.dtype == np.uint16:  # raw bfloat16 bits, widened exactly
+        vals = np.ascontiguousarray(p.values_f64(), dtype=np_dt[values_dtype])
+    elif values_dtype == "bf16":  # values already on the bf16 grid: keep the top 16 bits
         v32 = np.ascontiguousarray(p.values, dtype=np.float32).view(np.uint32)
         if np.any(v32 & 0xFFFF):
             raise ValueError("values are not exactly representable in bf16")
@@ -255,6 +267,11 @@ def asaga_autotune(ctx: int, trial_epochs: float = 0.0) -> dict:
 
 def asaga_set_schedule(ctx: int, warps: int, gamma: float, warps_per_block: int = 0) -> None:
     _check(ctx, load().asaga_set_schedule(ctx, int(warps), float(gamma), int(warps_per_block)))
+
+
+def asaga_set_row_path(ctx: int, threshold: int, group: int) -> None:
+    """Rows longer than `threshold` entries (0: all, -1: none) on cores of `group` warps."""
+    _check(ctx, load().asaga_set_row_path(ctx, int(threshold), int(group)))
 
 
 def asaga_cancel(ctx: int) -> None:
@@ -431,6 +448,17 @@ def asaga_batch_set_schedule(b: int, warps=None, gamma=None) -> None:
     _bcheck(b, load().asaga_batch_set_schedule(b, _ptr(w), _ptr(g)))
 
 
+def asaga_batch_set_row_paths(b: int, threshold, group) -> None:
+    t = np.ascontiguousarray(threshold, dtype=np.int64)
+    g = np.ascontiguousarray(group, dtype=np.int32)
+    _bcheck(b, load().asaga_batch_set_row_paths(b, _ptr(t), _ptr(g)))
+
+
+def asaga_batch_reset(b: int) -> None:
+    """Every instance back to x = 0 (the schedule stays)."""
+    _bcheck(b, load().asaga_batch_reset(b))
+
+
 def asaga_batch_get_state(b: int, i: int, d: int, n: int):
     x = np.empty(d, dtype=np.float32)
     abar = np.empty(d, dtype=np.float32)
@@ -459,9 +487,13 @@ def asaga_batch_destroy(b) -> None:
 class Batch:
     """Owning wrapper over a batch of generated problems."""
 
-    def __init__(self, problems, *, storage: str, values_dtype: str = "f64", per_instance=None, **options):
+    def __init__(self, problems, *, storage: str, values_dtype: str = "f64", per_instance=None, structs=None,
+                 **options):
+        """problems: generated problems (their loss and lambda set each
+        instance's options); structs: prebuilt asaga.Problem objects for them
+        (e.g. over device arrays), else host_problem(p, values_dtype)."""
         self.problems = problems
-        self.structs = [host_problem(p, values_dtype) for p in problems]
+        self.structs = structs if structs is not None else [host_problem(p, values_dtype) for p in problems]
         opts = []
         for k, p in enumerate(problems):
             o = dict(loss=p.loss, lam=p.lam, storage_dtype=storage, seed=k)

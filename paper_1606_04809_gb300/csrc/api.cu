@@ -41,6 +41,16 @@ struct asaga_ctx {
     bool plain_writes = false;
     int sampling = 0;              // ASAGA_SAMPLE_UNIFORM or ASAGA_SAMPLE_PERMUTATION
     bool spread = false;           // update kernel: warps spread over the SMs (else 8 per block)
+    // row paths: rows longer than row_threshold entries (0: all, < 0: none)
+    // are updated by cores of row_group warps (the multi-warp row path)
+    int row_group = 1;
+    int64_t row_threshold = -1;
+    uint32_t *long_bits = nullptr;   // bit i: row i is longer than bits_threshold
+    int64_t bits_threshold = -1;     // the threshold long_bits was built for (-1: not built)
+    double long_share = 0;           // fraction of the nonzeros in rows longer than bits_threshold
+    unsigned long long *d_sums = nullptr;
+    float *tail_c = nullptr;         // per-core scratch for entries past the register slots
+    int64_t tail_floats = 0;
     uint64_t seed = 0;
     int epochs_per_segment = 1;
     int abar_every = 0;
@@ -102,7 +112,12 @@ struct asaga_batch {
     std::vector<EvalParams> ev_full;              // every instance's evaluation parameters
     int *d_block_begin = nullptr;
     double *d_partial = nullptr, *d_f = nullptr, *h_f = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    double *d_rpartial = nullptr, *d_drift = nullptr, *h_drift = nullptr;  // the batched abar recomputation
+    int recompute_grid = 1;
+    int max_hot = 0;
+    int *d_status = nullptr, *h_status = nullptr;  // the update kernel's status bits of every instance
+    cudaGraphExec_t graph = nullptr;     // segment: update launch, objectives
+    cudaGraphExec_t graph_rc = nullptr;  // the same with the abar recomputation after the updates
     cudaEvent_t ev[2] = {nullptr, nullptr};
     int64_t launches = 0;
     std::string err;
@@ -424,6 +439,7 @@ EvalParams eval_params(const asaga_ctx *c) {
     e.hot_slot = c->hot_slot;
     e.hot_col = c->hot_col;
     e.n_hot = c->n_hot;
+    e.acc = c->acc64;
     return e;
 }
 
@@ -514,14 +530,14 @@ asaga_status apply_compact(asaga_ctx *c, bool rows_equal, bool idx16, std::strin
         c->layout = kRowScale;
     }
     if (idx16 && c->d <= 65536) {
-        // 64 bytes of slack: the update kernel stages 16-bit indices as aligned 32-bit words
+        // 64 bytes of slack: the update kernel copies row slices rounded out to 16-byte boundaries
         TRY(dev_alloc(&c->col16, (size_t)c->nnz + 32, c, err, "alloc 16-bit columns"));
         CK(launch_cols_to_u16(c->col_idx, c->col16, c->nnz, c->stream), "16-bit columns");
         ++c->launches;
         TRY(stream_sync(c, err));
         cudaFree(c->col_idx);
         c->col_idx = nullptr;
-        c->device_bytes -= (int64_t)(c->nnz * sizeof(int32_t));
+        c->device_bytes -= (int64_t)((c->nnz + 4) * sizeof(int32_t));
         c->layout |= kIdx16;
     }
     return ASAGA_OK;
@@ -566,13 +582,14 @@ asaga_status create_buffers(asaga_ctx *c, const asaga_problem *p, const asaga_op
     // problem
     if (!c->dense) {
         TRY(dev_alloc(&c->row_ptr, c->n + 1, c, err, "alloc row_ptr"));
-        TRY(dev_alloc(&c->col_idx, c->nnz, c, err, "alloc col_idx"));
+        // 16 bytes of slack: the update kernel copies row slices rounded out to 16-byte boundaries
+        TRY(dev_alloc(&c->col_idx, c->nnz + 4, c, err, "alloc col_idx"));
         CK(cudaMemcpyAsync(c->row_ptr, p->row_ptr, (c->n + 1) * sizeof(int64_t), kind, c->stream), "copy row_ptr");
         if (c->nnz > 0)
             CK(cudaMemcpyAsync(c->col_idx, p->col_idx, c->nnz * sizeof(int32_t), kind, c->stream), "copy col_idx");
     }
     unsigned char *vals = nullptr;
-    // 64 bytes of slack: the update kernel stages 16-bit values as aligned 32-bit words
+    // 64 bytes of slack: the update kernel copies row slices rounded out to 16-byte boundaries
     TRY(dev_alloc(&vals, (size_t)c->nnz * vsz + 64, c, err, "alloc values"));
     c->values = vals;
     const int in_dt = (int)p->values_dtype;
@@ -745,6 +762,9 @@ void release(asaga_ctx *c) {
     cudaFree(c->idx_buf);
     cudaFree(c->hot_slot);
     cudaFree(c->hot_col);
+    cudaFree(c->long_bits);
+    cudaFree(c->d_sums);
+    cudaFree(c->tail_c);
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstatus) cudaFreeHost(c->hstatus);
     if (c->h_cancel) cudaFreeHost(c->h_cancel);
@@ -757,6 +777,7 @@ void release(asaga_ctx *c) {
 
 UpdateParams update_params(const asaga_ctx *c) {
     UpdateParams u;
+    std::memset(&u, 0, sizeof(u));
     u.n = c->n;
     u.d = c->d;
     u.nnz = c->nnz;
@@ -774,7 +795,15 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.seed = c->seed;
     u.t_begin = 0;
     u.count = 0;
-    u.nwarps = c->warps;
+    u.short_cores = c->warps;  // concurrent updates; split between the row paths at launch
+    u.long_cores = 0;
+    u.group = 1;
+    u.threshold = -1;
+    u.wpb = 1;
+    u.short_blocks = 0;
+    u.long_bits = nullptr;
+    u.tail_c = nullptr;
+    u.tail_stride = 0;
     u.idx = nullptr;
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.plain_writes = c->plain_writes ? 1 : 0;
@@ -786,22 +815,129 @@ UpdateParams update_params(const asaga_ctx *c) {
     return u;
 }
 
-int update_warps_per_block(const asaga_ctx *c, int nwarps) {
-    if (nwarps <= 1) return 1;
-    const int per_sm = (nwarps + c->sms - 1) / std::max(1, c->sms);
-    return c->spread ? std::min(kUpdateBlock / 32, std::max(1, per_sm)) : kUpdateBlock / 32;
+// Bits of the rows longer than `threshold` entries and the share of the
+// nonzeros they hold (built once per threshold).
+asaga_status ensure_row_classes(asaga_ctx *c, int64_t threshold, std::string *err) {
+    if (c->bits_threshold == threshold && c->long_bits) return ASAGA_OK;
+    if (c->dense) {  // every row has d entries
+        c->long_share = c->d > threshold ? 1.0 : 0.0;
+        c->bits_threshold = threshold;
+        return ASAGA_OK;
+    }
+    if (!c->long_bits) TRY(dev_alloc(&c->long_bits, (size_t)((c->n + 31) / 32), c, err, "alloc row classes"));
+    if (!c->d_sums) TRY(dev_alloc(&c->d_sums, 2, c, err, "alloc row class sums"));
+    CK(cudaMemsetAsync(c->d_sums, 0, 2 * sizeof(unsigned long long), c->stream), "memset");
+    CK(launch_row_classes(c->row_ptr, c->n, threshold, c->long_bits, c->d_sums, c->stream), "row classes");
+    ++c->launches;
+    unsigned long long h[2] = {0, 0};
+    CK(cudaMemcpyAsync(h, c->d_sums, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy row class sums");
+    TRY(stream_sync(c, err));
+    c->long_share = c->nnz > 0 ? (double)h[0] / (double)c->nnz : 0.0;
+    c->bits_threshold = threshold;
+    return ASAGA_OK;
 }
 
+// How a launch of W warps is laid out on the device: the split of the
+// warps between single-warp and multi-warp cores, the block shape and the
+// scratch for entries past the register slots.
+struct CoreLayout {
+    int short_cores = 0, long_cores = 0, group = 1, wpb = 8, short_blocks = 0, grid = 0;
+    int64_t threshold = -1;
+    int64_t tail_stride = 0;
+    bool both = false;  // both paths in use (the row classes decide)
+};
+
+// Layout of W warps under the row path (threshold, group).  The row path
+// regroups the warps into cores and keeps their number: measured on a
+// GB300, the stability frontier of the asynchronous iteration lies at a
+// product of total warps and step, not of concurrent updates (cores of 4
+// warps at the cores x step of a converging single-warp run stalled on a
+// plateau; at the same warps x step they converged).  With both paths the
+// long rows' cores get the share of the warps that their rows hold of the
+// nonzeros (long_share; ensure_row_classes must have run).  serial: one
+// core, strictly in order (only one path can then apply).
+CoreLayout core_layout(const asaga_ctx *c, int W, int64_t threshold, int group, bool serial) {
+    CoreLayout L;
+    if (group <= 1 || threshold >= c->max_row_len) threshold = -1;  // no row takes the multi-warp path
+    if (serial && threshold > 0) threshold = -1;
+    if (threshold > 0 && W < group + 1) threshold = -1;
+    L.threshold = threshold;
+    L.group = threshold < 0 ? 1 : group;
+    const int G = L.group;
+    if (threshold < 0) {
+        L.short_cores = W;
+    } else if (threshold == 0) {
+        L.long_cores = serial ? 1 : std::max(1, W / G);
+    } else {
+        L.both = true;
+        int wl = (int)std::llround((double)W * c->long_share);
+        wl = std::max(G, std::min(W - 1, wl));
+        L.long_cores = std::max(1, wl / G);
+        L.short_cores = std::max(1, W - L.long_cores * G);
+    }
+    const int warps = L.short_cores + L.long_cores * G;
+    const int per_sm = (warps + c->sms - 1) / std::max(1, c->sms);
+    int wpb = warps <= 1 ? 1 : (c->spread ? std::min(kUpdateBlock / 32, std::max(1, per_sm)) : kUpdateBlock / 32);
+    wpb = std::max(wpb, G);
+    wpb = (wpb + G - 1) / G * G;
+    if (L.short_cores + L.long_cores <= 1) wpb = G;  // one core
+    L.wpb = wpb;
+    L.short_blocks = (L.short_cores + wpb - 1) / wpb;
+    const int cpb = wpb / G;
+    L.grid = L.short_blocks + (L.long_cores + cpb - 1) / cpb;
+    // register capacity of a core: 32 x warps x slots entries
+    const int slots = update_register_slots(c->dense, false);
+    int64_t need = 0;
+    if (L.short_cores > 0) {
+        const int64_t longest = L.threshold > 0 ? std::min(L.threshold, c->max_row_len) : c->max_row_len;
+        need = std::max<int64_t>(need, longest - 32 * slots);
+    }
+    if (L.long_cores > 0) need = std::max<int64_t>(need, c->max_row_len - (int64_t)32 * G * slots);
+    L.tail_stride = need;
+    return L;
+}
+
+int update_warps_per_block(const asaga_ctx *c, int nwarps) {
+    return core_layout(c, nwarps, c->row_threshold, c->row_group, nwarps <= 1).wpb;
+}
+
+// Launches the updates on u.short_cores warps (the callers' "warps"),
+// grouped into cores by the context's row path, in its block shape.
 asaga_status launch_updates(asaga_ctx *c, UpdateParams u, std::string *err) {
     // eight warps to a block, or (c->spread) the warps spread evenly over
     // the SMs, one block per SM while they allow: then each SM's load/store
     // units and outstanding misses serve fewer warps, which helps a
     // latency-bound state larger than L2 and not a small hot-line-bound one
     // (the autotuner times both)
-    const int wpb = update_warps_per_block(c, u.nwarps);
-    const int block = 32 * wpb;
-    const int grid = (u.nwarps + wpb - 1) / wpb;
-    CK(launch_update(u, c->layout, c->dense, grid, block, c->stream), "update kernel");
+    const int C = u.short_cores;
+    const bool serial = u.fence_each != 0 || u.idx != nullptr;
+    const CoreLayout L = core_layout(c, C, c->row_threshold, c->row_group, serial);
+    if (L.both) TRY(ensure_row_classes(c, L.threshold, err));
+    const CoreLayout M = L.both ? core_layout(c, C, c->row_threshold, c->row_group, serial) : L;  // with the share
+    u.short_cores = M.short_cores;
+    u.long_cores = M.long_cores;
+    u.group = M.group;
+    u.threshold = M.threshold;
+    u.wpb = M.wpb;
+    u.short_blocks = M.short_blocks;
+    u.long_bits = M.both ? c->long_bits : nullptr;
+    if (M.tail_stride > 0) {
+        const int64_t need = (int64_t)(M.short_cores + M.long_cores) * M.tail_stride;
+        if (need > c->tail_floats) {
+            CK(cudaStreamSynchronize(c->stream), "sync");
+            if (c->tail_c) {
+                cudaFree(c->tail_c);
+                c->device_bytes -= c->tail_floats * (int64_t)sizeof(float);
+                c->tail_c = nullptr;
+                c->tail_floats = 0;
+            }
+            TRY(dev_alloc(&c->tail_c, (size_t)need, c, err, "alloc row tail scratch"));
+            c->tail_floats = need;
+        }
+        u.tail_c = c->tail_c;
+        u.tail_stride = M.tail_stride;
+    }
+    CK(launch_update(u, c->layout, c->dense, M.grid, c->stream), "update kernel");
     ++c->launches;
     return ASAGA_OK;
 }
@@ -871,6 +1007,12 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
             fail(err, st, "update kernel found a malformed row range");
             break;
         }
+        if (*c->hstatus & 48) {
+            st = ASAGA_ECUDA;
+            fail(err, st, (*c->hstatus & 16) ? "update kernel: a row's staging copy did not complete in time"
+                                             : "update kernel: row scratch smaller than a row");
+            break;
+        }
         if (*c->hstatus & 1) {
             st = ASAGA_ETIMEOUT;
             fail(err, st, "timeout");
@@ -930,11 +1072,12 @@ asaga_status enqueue_grad(asaga_ctx *c, std::string *err) {
 // kernel's device time and |grad f|^2 after it.
 asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, double *g2, std::string *err) {
     UpdateParams u = update_params(c);
-    u.nwarps = warps;
+    u.short_cores = warps;
     u.fence_each = warps == 1;
     u.gamma = (float)gamma;
     u.t_begin = (uint64_t)c->updates_done;
     u.count = c->n;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream), "memset status");
     CK(cudaEventRecord(c->ev[0], c->stream), "event");
     TRY(launch_updates(c, u, err));
     CK(cudaEventRecord(c->ev[1], c->stream), "event");
@@ -943,7 +1086,9 @@ asaga_status trial_epoch(asaga_ctx *c, int warps, double gamma, double *ms, doub
         TRY(enqueue_grad(c, err));
         CK(cudaMemcpyAsync(c->hout + 2, c->dout + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy");
     }
+    CK(cudaMemcpyAsync(c->hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
     TRY(stream_sync(c, err));
+    if (*c->hstatus & 52) return fail(err, ASAGA_ECUDA, "update kernel status " + std::to_string(*c->hstatus));
     float f = 0;
     cudaEventElapsedTime(&f, c->ev[0], c->ev[1]);
     *ms = f;
@@ -1066,10 +1211,51 @@ asaga_status tune_trial(asaga_ctx *c, int W, double gamma, double g0, int E, dou
     return trial_epochs_run(c, W, gamma, g0, E, stop_level, give_up_ms, out, err);
 }
 
+// Row paths worth timing for a problem: multi-warp cores of G = 2, 4, 8
+// warps, for every row (T = 0) when the mean row fills the G warps' lanes,
+// or for the rows longer than T = 128, 256, 512 entries when those hold at
+// least 2% of the nonzeros.
+asaga_status row_path_candidates(asaga_ctx *c, std::vector<std::pair<int64_t, int>> *out, std::string *err) {
+    out->clear();
+    const double mean_len = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+    for (int G : {2, 4, 8}) {
+        if ((int64_t)32 * G > c->max_row_len) continue;
+        if (mean_len >= 32.0 * G) out->push_back({0, G});
+        if (c->dense) continue;
+        for (int64_t T : {128, 256, 512}) {
+            if (T >= c->max_row_len || T < 32 * G) continue;
+            TRY(ensure_row_classes(c, T, err));
+            if (c->long_share < 0.02) continue;
+            out->push_back({T, G});
+        }
+    }
+    return ASAGA_OK;
+}
+
+// Epoch time of the row path (T, G) at (warps, gamma): the faster of two
+// epochs after one untimed, from x = 0.
+asaga_status time_row_path(asaga_ctx *c, int warps, double gamma, int64_t T, int G, double *ms_out, double *seconds,
+                           std::string *err) {
+    c->row_threshold = T;
+    c->row_group = G;
+    TRY(reset_state(c, err));
+    double best = INFINITY;
+    for (int e = 0; e < 3; ++e) {
+        double ms = 0;
+        TRY(trial_epoch(c, warps, gamma, &ms, nullptr, err));
+        *seconds += ms * 1e-3;
+        if (e > 0) best = std::min(best, ms);
+    }
+    *ms_out = best;
+    return ASAGA_OK;
+}
+
 asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result *res, std::string *err) {
     NvtxRange range("asaga_autotune");
     if (c->deterministic) return fail(err, ASAGA_EINVAL, "autotune needs asynchronous mode");
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
+    c->row_threshold = -1;  // the trials run on single-warp cores; the row path comes last
+    c->row_group = 1;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const int E_race = trial_epochs > 0 ? std::max(4, (int)std::ceil(trial_epochs)) : 24;
     const int E_probe = std::min(16, E_race);
@@ -1228,9 +1414,51 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         }
         c->spread = t_shape[1] < 0.98 * t_shape[0];
     }
+    // 5. the row path at the winner (the same warps and step, regrouped into
+    //    cores): rows longer than T entries on cores of G warps, for the
+    //    (T, G) of row_path_candidates, timed; the two fastest that beat
+    //    single warps by 3% then run a race trial, and the first whose
+    //    predicted time beats the winner's by 3% is kept (a plateau has no
+    //    prediction)
+    c->row_threshold = -1;
+    c->row_group = 1;
+    if (std::isfinite(best_ms)) {
+        std::vector<std::pair<int64_t, int>> cand;
+        TRY(row_path_candidates(c, &cand, err));
+        if (!cand.empty()) {
+            double t_single = INFINITY;
+            TRY(time_row_path(c, best_w, step(best_k), -1, 1, &t_single, &r.seconds, err));
+            std::vector<std::pair<double, size_t>> order;
+            for (size_t j = 0; j < cand.size(); ++j) {
+                double t = INFINITY;
+                TRY(time_row_path(c, best_w, step(best_k), cand[j].first, cand[j].second, &t, &r.seconds, err));
+                if (t < 0.97 * t_single) order.push_back({t, j});
+            }
+            std::sort(order.begin(), order.end());
+            int64_t keep_T = -1;
+            int keep_G = 1;
+            for (size_t o = 0; o < order.size() && o < 2; ++o) {
+                c->row_threshold = cand[order[o].second].first;
+                c->row_group = cand[order[o].second].second;
+                TuneTrial t;
+                TRY(run(best_w, best_k, E_race, kTuneDeep, 1.5 * best_ms, &t));
+                const double ms = predict_epochs(t) * t.ms_per_epoch();
+                if (!t.diverged && std::isfinite(ms) && ms < 0.97 * best_ms) {
+                    keep_T = c->row_threshold;
+                    keep_G = c->row_group;
+                    best_ms = ms;
+                    break;
+                }
+            }
+            c->row_threshold = keep_T;
+            c->row_group = keep_G;
+        }
+    }
     if (std::isfinite(best_ms)) r.score = 1e3 / best_ms;
     r.warps = best_w;
     r.gamma = step(best_k);
+    r.row_threshold = c->row_threshold;
+    r.row_group = c->row_group;
     TRY(reset_state(c, err));
     c->warps = r.warps;
     c->gamma = r.gamma;
@@ -1334,7 +1562,7 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
         didx = c->idx_buf;
     }
     UpdateParams u = update_params(c);
-    u.nwarps = 1;
+    u.short_cores = 1;
     u.fence_each = 1;
     u.idx = didx;
     u.count = count;
@@ -1343,6 +1571,7 @@ asaga_status run_indices_impl(asaga_ctx *c, const int64_t *idx, int64_t count, i
     CK(cudaMemcpyAsync(c->hstatus, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy status");
     TRY(stream_sync(c, err));
     if (*c->hstatus & 2) return fail(err, ASAGA_EINVAL, "index out of range in device index array");
+    if (*c->hstatus & 52) return fail(err, ASAGA_ECUDA, "update kernel status " + std::to_string(*c->hstatus));
     return ASAGA_OK;
 }
 
@@ -1352,7 +1581,13 @@ void batch_release(asaga_batch *b) {
     if (!b) return;
     if (b->stream) cudaStreamSynchronize(b->stream);
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_rc) cudaGraphExecDestroy(b->graph_rc);
     for (auto *c : b->ctx) release(c);
+    cudaFree(b->d_rpartial);
+    cudaFree(b->d_drift);
+    cudaFree(b->d_status);
+    if (b->h_drift) cudaFreeHost(b->h_drift);
+    if (b->h_status) cudaFreeHost(b->h_status);
     cudaFree(b->d_up);
     cudaFree(b->d_ev);
     cudaFree(b->d_block_begin);
@@ -1368,14 +1603,66 @@ void batch_release(asaga_batch *b) {
     delete b;
 }
 
-// Lays the schedule out: instance i owns warps[i]/4 consecutive blocks.
+// Lays the schedule out: instance i owns warps[i]/4 consecutive blocks of 4
+// warps, holding 4 single-warp cores each or, on its multi-warp row path,
+// 4/G cores of G warps (G <= 4); with both paths in use the blocks are
+// split by the share of the nonzeros in the long rows.
 asaga_status batch_layout(asaga_batch *b, std::string *err) {
     b->block_begin.assign(b->count, 0);
     int g = 0;
+    const int slots = update_register_slots(b->dense, true);
     for (int i = 0; i < b->count; ++i) {
+        asaga_ctx *c = b->ctx[i];
+        const int blocks = std::max(1, b->warps[i] / 4);
         b->block_begin[i] = g;
-        g += std::max(1, b->warps[i] / 4);
-        b->h_up[i].nwarps = std::max(1, b->warps[i] / 4) * 4;
+        g += blocks;
+        UpdateParams &u = b->h_up[i];
+        int G = std::min(c->row_group, 4);
+        int64_t T = c->row_threshold;
+        if (G <= 1 || T >= c->max_row_len) T = -1;
+        if (T > 0 && blocks < 2) T = -1;
+        if (T < 0) G = 1;
+        u.wpb = 4;
+        u.group = G;
+        u.threshold = T;
+        u.long_bits = nullptr;
+        if (T < 0) {
+            u.short_blocks = blocks;
+            u.short_cores = 4 * blocks;
+            u.long_cores = 0;
+        } else if (T == 0) {
+            u.short_blocks = 0;
+            u.short_cores = 0;
+            u.long_cores = blocks * (4 / G);
+        } else {
+            TRY(ensure_row_classes(c, T, err));
+            const int lb = std::max(1, std::min(blocks - 1, (int)std::llround(blocks * c->long_share)));
+            u.short_blocks = blocks - lb;
+            u.short_cores = 4 * u.short_blocks;
+            u.long_cores = lb * (4 / G);
+            u.long_bits = c->long_bits;
+        }
+        int64_t need = 0;
+        if (u.short_cores > 0) need = (T > 0 ? std::min(T, c->max_row_len) : c->max_row_len) - 32 * slots;
+        if (u.long_cores > 0) need = std::max<int64_t>(need, c->max_row_len - (int64_t)32 * G * slots);
+        u.tail_c = nullptr;
+        u.tail_stride = 0;
+        if (need > 0) {
+            const int64_t floats = (int64_t)(u.short_cores + u.long_cores) * need;
+            if (floats > c->tail_floats) {
+                CK(cudaStreamSynchronize(b->stream), "sync");
+                if (c->tail_c) {
+                    cudaFree(c->tail_c);
+                    c->device_bytes -= c->tail_floats * (int64_t)sizeof(float);
+                    c->tail_c = nullptr;
+                    c->tail_floats = 0;
+                }
+                TRY(dev_alloc(&c->tail_c, (size_t)floats, c, err, "alloc row tail scratch"));
+                c->tail_floats = floats;
+            }
+            u.tail_c = c->tail_c;
+            u.tail_stride = need;
+        }
     }
     b->grid = g;
     CK(cudaMemcpyAsync(b->d_block_begin, b->block_begin.data(), b->count * sizeof(int), cudaMemcpyHostToDevice,
@@ -1383,6 +1670,10 @@ asaga_status batch_layout(asaga_batch *b, std::string *err) {
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
+    }
+    if (b->graph_rc) {
+        cudaGraphExecDestroy(b->graph_rc);
+        b->graph_rc = nullptr;
     }
     return ASAGA_OK;
 }
@@ -1490,13 +1781,23 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
     TRY(dev_alloc(&b->d_block_begin, count, b->ctx[0], err, "alloc schedule"));
     TRY(dev_alloc(&b->d_partial, 2 * (size_t)count * b->eval_grid, b->ctx[0], err, "alloc partials"));
     TRY(dev_alloc(&b->d_f, count, b->ctx[0], err, "alloc objectives"));
+    b->recompute_grid = std::max(1, std::min(64, (prop.multiProcessorCount * 8 + count - 1) / count));
+    TRY(dev_alloc(&b->d_rpartial, (size_t)count * b->recompute_grid, b->ctx[0], err, "alloc partials"));
+    TRY(dev_alloc(&b->d_drift, count, b->ctx[0], err, "alloc drifts"));
+    TRY(dev_alloc(&b->d_status, 1, b->ctx[0], err, "alloc status"));
+    CK(cudaMemsetAsync(b->d_status, 0, sizeof(int), b->stream), "memset status");
+    CK(cudaMallocHost((void **)&b->h_drift, count * sizeof(double)), "alloc pinned");
+    CK(cudaMallocHost((void **)&b->h_status, sizeof(int)), "alloc pinned");
+    *b->h_status = 0;
     std::vector<EvalParams> ev(count);
     for (int i = 0; i < count; ++i) {
         b->h_up[i] = update_params(b->ctx[i]);
         b->h_up[i].count = 0;
         b->h_up[i].fence_each = 0;
+        b->h_up[i].status = b->d_status;  // one status word for the whole batch
         ev[i] = eval_params(b->ctx[i]);
         b->h_ev[i] = ev[i];
+        b->max_hot = std::max(b->max_hot, b->ctx[i]->n_hot);
     }
     b->ev_full = ev;
     CK(cudaMemcpyAsync(b->d_ev, ev.data(), count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
@@ -1506,42 +1807,56 @@ asaga_status batch_create_impl(asaga_batch *b, int count, const asaga_problem *p
 }
 
 // Enqueues one segment: parameters in, one update launch over all
-// instances, the batched objective, objectives out.
-asaga_status batch_enqueue_segment(asaga_batch *b, std::string *err) {
+// instances, (every abar_recompute_every-th segment) the batched abar
+// recomputation, the batched objective, objectives, drifts and status out.
+asaga_status batch_enqueue_segment(asaga_batch *b, bool recompute, std::string *err) {
     CK(cudaMemcpyAsync(b->d_up, b->h_up, b->count * sizeof(UpdateParams), cudaMemcpyHostToDevice, b->stream),
        "copy params");
-    CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->layout, b->dense, b->stream),
-       "batch update kernel");
     CK(cudaMemcpyAsync(b->d_ev, b->h_ev, b->count * sizeof(EvalParams), cudaMemcpyHostToDevice, b->stream),
        "copy eval params");
+    CK(launch_batch_update(b->d_up, b->d_block_begin, b->count, b->grid, b->layout, b->dense, b->stream),
+       "batch update kernel");
+    if (recompute) {
+        CK(launch_batch_recompute(b->d_ev, b->count, b->recompute_grid, b->layout, b->dense, b->max_hot,
+                                  b->d_rpartial, b->d_drift, b->stream),
+           "batch abar recomputation");
+        CK(cudaMemcpyAsync(b->h_drift, b->d_drift, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream),
+           "copy drift");
+    }
     CK(launch_batch_objective(b->d_ev, b->count, b->eval_grid, b->layout, b->dense, b->d_partial, b->d_f, b->stream),
        "batch objective");
     CK(cudaMemcpyAsync(b->h_f, b->d_f, b->count * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "copy f");
+    CK(cudaMemcpyAsync(b->h_status, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, b->stream), "copy status");
     return ASAGA_OK;
 }
 
-// Runs one segment through the captured graph (captured on first use).
-asaga_status batch_segment(asaga_batch *b, float *ms, std::string *err) {
-    if (!b->graph) {
+// Runs one segment through its captured graph (captured on first use; one
+// graph without and one with the abar recomputation).  *ms: the segment's
+// device time, recomputation included.
+asaga_status batch_segment(asaga_batch *b, bool recompute, float *ms, std::string *err) {
+    cudaGraphExec_t &exec = recompute ? b->graph_rc : b->graph;
+    if (!exec) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        asaga_status st = batch_enqueue_segment(b, err);
+        asaga_status st = batch_enqueue_segment(b, recompute, err);
         cudaError_t e = cudaStreamEndCapture(b->stream, &g);
         if (st != ASAGA_OK) {
             if (g) cudaGraphDestroy(g);
             return st;
         }
         if (e != cudaSuccess) return cuda_fail(err, e, "end capture");
-        e = cudaGraphInstantiate(&b->graph, g, 0);
+        e = cudaGraphInstantiate(&exec, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return cuda_fail(err, e, "graph instantiate");
     }
     CK(cudaEventRecord(b->ev[0], b->stream), "event");
-    CK(cudaGraphLaunch(b->graph, b->stream), "graph launch");
+    CK(cudaGraphLaunch(exec, b->stream), "graph launch");
     CK(cudaEventRecord(b->ev[1], b->stream), "event");
-    b->launches += 3;
+    b->launches += recompute ? 7 : 3;
     CK(cudaStreamSynchronize(b->stream), "stream synchronize");
     cudaEventElapsedTime(ms, b->ev[0], b->ev[1]);
+    if (*b->h_status & 52)
+        return fail(err, ASAGA_ECUDA, "batch update kernel status " + std::to_string(*b->h_status));
     return ASAGA_OK;
 }
 
@@ -1585,8 +1900,11 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
             b->h_ev[i] = b->ev_full[i];
             if (!active[i]) b->h_ev[i].n = b->h_ev[i].d = 0;
         }
+        // every abar_recompute_every-th segment of the batch, counted across calls
+        const bool recompute = b->abar_every > 0 && (b->segments_done + 1) % b->abar_every == 0;
         float ms = 0;
-        TRY(batch_segment(b, &ms, err));
+        TRY(batch_segment(b, recompute, &ms, err));
+        ++b->segments_done;
         elapsed_ms += ms;
         epochs += ep;
         ++seg;
@@ -1599,6 +1917,7 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
             r[i].segments = seg;
             r[i].f_last = b->h_f[i];
             r[i].solver_seconds = elapsed_ms * 1e-3;  // device time of the shared segments
+            if (recompute) r[i].abar_drift = b->h_drift[i];
             if (f_star) r[i].rel_subopt = (r[i].f_last - f_star[i]) / std::fabs(f_star[i]);
             const bool diverged = !std::isfinite(r[i].f_last);
             const bool reached = target > 0 && r[i].rel_subopt <= target;
@@ -1606,11 +1925,6 @@ asaga_status batch_run_impl(asaga_batch *b, double max_epochs, double target, co
                 active[i] = 0;
                 --n_active;
             }
-        }
-        if (b->abar_every > 0 && ++b->segments_done % b->abar_every == 0) {  // counted across calls
-            for (int i = 0; i < b->count; ++i)
-                if (active[i]) TRY(enqueue_recompute(b->ctx[i], err));
-            TRY(stream_sync(b->ctx[0], err));
         }
     }
     for (int i = 0; i < b->count; ++i) b->h_ev[i] = b->ev_full[i];  // later segments evaluate every instance
@@ -1675,7 +1989,7 @@ asaga_status batch_tune_pass(asaga_batch *b, int E, std::vector<int> *kc_out, st
                 b->h_up[i].count = c->n;
             }
             float ms = 0;
-            TRY(batch_segment(b, &ms, err));
+            TRY(batch_segment(b, false, &ms, err));
             *seconds += ms * 1e-3;
             for (auto *c : b->ctx) c->updates_done += c->n;
             TRY(grads(g));
@@ -1764,7 +2078,7 @@ asaga_status batch_refine_predictions(asaga_batch *b, int E, const std::vector<i
         }
         if (!any) break;
         float ms = 0;
-        TRY(batch_segment(b, &ms, err));
+        TRY(batch_segment(b, false, &ms, err));
         *seconds += ms * 1e-3;
         for (int i : slow) {
             if (!live[i]) continue;
@@ -2060,6 +2374,18 @@ asaga_status asaga_set_schedule(asaga_ctx *c, int warps, double gamma, int warps
     return ASAGA_OK;
 }
 
+asaga_status asaga_set_row_path(asaga_ctx *c, int64_t threshold, int group) {
+    if (!c) return ASAGA_EINVAL;
+    if (group != 1 && group != 2 && group != 4 && group != 8)
+        return fail(&c->err, ASAGA_EINVAL, "group must be 1, 2, 4 or 8");
+    if (threshold < -1) return fail(&c->err, ASAGA_EINVAL, "threshold must be >= -1");
+    if (c->deterministic && threshold > 0)
+        return fail(&c->err, ASAGA_EINVAL, "deterministic mode takes one path (threshold -1 or 0)");
+    c->row_threshold = group > 1 ? threshold : -1;
+    c->row_group = threshold >= 0 ? group : 1;
+    return ASAGA_OK;
+}
+
 asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     if (!c || !info) return ASAGA_EINVAL;
     info->n = c->n;
@@ -2076,6 +2402,8 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->warps_per_block = update_warps_per_block(c, c->warps);
     info->col_index_bytes = c->dense ? 0 : ((c->layout & kIdx16) ? 2 : 4);
     info->row_values = (c->layout & ~kIdx16) == kRowScale ? 1 : 0;
+    info->row_threshold = c->row_threshold;
+    info->row_group = c->row_group;
     return ASAGA_OK;
 }
 
@@ -2142,6 +2470,31 @@ asaga_status asaga_batch_set_schedule(asaga_batch *b, const int *warps, const do
             b->ctx[i]->gamma = gamma[i];
         }
     return ASAGA_OK;
+}
+
+asaga_status asaga_batch_set_row_paths(asaga_batch *b, const int64_t *threshold, const int *group) {
+    if (!b) return ASAGA_EINVAL;
+    std::string *err = &b->err;
+    if (!threshold || !group) return fail(err, ASAGA_EINVAL, "threshold and group must not be NULL");
+    for (int i = 0; i < b->count; ++i) {
+        if (group[i] != 1 && group[i] != 2 && group[i] != 4)
+            return fail(err, ASAGA_EINVAL, "group must be 1, 2 or 4 (blocks of 4 warps)");
+        if (threshold[i] < -1) return fail(err, ASAGA_EINVAL, "threshold must be >= -1");
+    }
+    for (int i = 0; i < b->count; ++i) {
+        b->ctx[i]->row_threshold = group[i] > 1 ? threshold[i] : -1;
+        b->ctx[i]->row_group = threshold[i] >= 0 ? group[i] : 1;
+    }
+    return batch_layout(b, err);
+}
+
+asaga_status asaga_batch_reset(asaga_batch *b) {
+    if (!b) return ASAGA_EINVAL;
+    std::string *err = &b->err;
+    CK(cudaSetDevice(b->device), "cudaSetDevice");
+    for (auto *c : b->ctx) TRY(reset_state(c, err));
+    b->segments_done = 0;
+    return stream_sync(b->ctx[0], err);
 }
 
 asaga_status asaga_batch_get_state(asaga_batch *b, int i, float *x, float *abar, float *alpha) {

@@ -26,6 +26,17 @@ constexpr int kIdx16 = 8;
 
 // Launch parameters of the asynchronous update kernel (one update = one
 // sampled row, Algorithm 2).
+//
+// Cores.  Each concurrent update runs on one "core": a single warp, or, on
+// the multi-warp row path, a group of `group` warps of one block that split
+// the row's entries, add their partial dot products through shared memory
+// and apply the same delta.  Rows longer than `threshold` entries take the
+// multi-warp path (threshold 0: every row; < 0: none).  Blocks
+// [0, short_blocks) hold `wpb` single-warp cores each and the others
+// wpb / group multi-warp cores; core j of a path takes the updates
+// t = j, j + cores, j + 2 cores, ... of the launch whose rows belong to that
+// path (long_bits tells a row's path when both paths are in use), so every
+// update is applied exactly once whatever the split.
 struct UpdateParams {
     int64_t n, d;
     int64_t nnz;              // entries of A (n*d for dense); staged row ranges are checked against it
@@ -42,13 +53,22 @@ struct UpdateParams {
     int sampling;             // 0 uniform with replacement, 1 one permutation per epoch
     uint64_t t_begin;         // global index of this launch's first update
     int64_t count;            // updates in this launch
-    int nwarps;               // warps taking part (static strided split)
+    int short_cores;          // single-warp cores
+    int long_cores;           // multi-warp cores (group warps each)
+    int group;                // warps per multi-warp core: 1, 2, 4 or 8
+    int64_t threshold;        // rows longer than this take the multi-warp path (0: all, < 0: none)
+    int wpb;                  // warps per block (a multiple of group)
+    int short_blocks;         // blocks of single-warp cores (the first ones)
+    const uint32_t *long_bits;  // bit i set: row i takes the multi-warp path; nullptr when one path takes all rows
+    float *tail_c;            // per core tail_stride floats: the update's term D_v (abar_v + lambda x^_v) for
+    int64_t tail_stride;      //   entries past the register slots (nullptr / 0 when no row has such entries)
     const int64_t *idx;       // explicit row sequence (deterministic replay) or nullptr
-    int fence_each;           // 1: fence after every update (single-warp order)
+    int fence_each;           // 1: fence after every update (single-core order)
     int plain_writes;         // 1: non-atomic load-add-store instead of reductions (diagnostic)
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     const volatile int *cancel;  // nonzero: stop (a flag in mapped host memory), or nullptr
-    int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range, bit 3: cancelled
+    int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range, bit 3: cancelled,
+                              // bit 4: a staging copy did not complete in time, bit 5: tail scratch too small
     uint64_t *trace;          // 2 * count: %globaltimer before the reads / after the writes of update t (or nullptr)
 };
 
@@ -67,10 +87,12 @@ struct EvalParams {
     const int *hot_slot;      // d entries: shared-memory slot of a frequent column, -1 otherwise (may be nullptr)
     const int *hot_col;       // n_hot entries: column of each slot
     int n_hot;
+    double *acc;              // d float64 accumulators (the batched abar recomputation)
 };
 
 constexpr int kUpdateBlock = 256;  // threads per block of the update kernel
 constexpr int kBatchBlock = 128;   // threads per block of the batched update kernel (4 warps)
+constexpr int kMaxGroup = 8;       // warps of the widest multi-warp core
 constexpr int kEvalBlock = 256;
 constexpr int kMaxPartials = 4096; // max blocks of the float64 row kernels
 constexpr int kMaxHot = 2048;      // frequent columns accumulated per block in shared memory
@@ -82,9 +104,18 @@ void set_thread_error(const std::string &msg);
 // rows[j] = the row of update t_begin + j (device buffer of count entries)
 cudaError_t launch_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t t_begin, int64_t count,
                                int64_t *rows, cudaStream_t stream);
-cudaError_t launch_update(const UpdateParams &p, int layout, bool dense, int grid, int block,
-                          cudaStream_t s);
+// grid = short_blocks + blocks of multi-warp cores, p.wpb warps per block.
+cudaError_t launch_update(const UpdateParams &p, int layout, bool dense, int grid, cudaStream_t s);
+// dynamic shared memory of an update block of wpb warps
+size_t update_smem_bytes(int wpb);
 int update_max_blocks_per_sm(int layout, bool dense);
+// register slots of 32 entries per lane of the update kernels: a core of g
+// warps keeps 32 g update_register_slots(...) entries of a row in registers
+int update_register_slots(bool dense, bool batch);
+// bits[i / 32] bit i % 32 <- (row_ptr[i+1] - row_ptr[i] > threshold); sums[0] += entries of
+// such rows, sums[1] += their number (sums: 2 int64, zeroed by the caller)
+cudaError_t launch_row_classes(const int64_t *row_ptr, int64_t n, int64_t threshold, uint32_t *bits,
+                               unsigned long long *sums, cudaStream_t s);
 // params[count] and block_begin[count] in device memory; instance i owns blocks
 // [block_begin[i], block_begin[i+1]) (the last one up to grid).
 cudaError_t launch_batch_update(const UpdateParams *params, const int *block_begin, int count, int grid, int layout,
@@ -112,6 +143,14 @@ cudaError_t launch_column_finish(const EvalParams &p, int mode, int grid, double
 // out[0] <- sum (mode 0) or max (mode 1) of partial[0..grid).
 cudaError_t launch_reduce_partials(const double *partial, int grid, int mode, double *out,
                                    cudaStream_t s);
+
+// The abar recomputation of `count` instances in three launches:
+// acc_i <- 0, acc_i[v] += sum_r (alpha_r / n_i) a_rv (a warp per row, grid x
+// count blocks), then abar_v <- (float)acc_v and drift_out[i] <- max_v
+// |abar_v(before) - acc_v|.  An instance with n = d = 0 is skipped.
+// partial holds grid * count doubles.
+cudaError_t launch_batch_recompute(const EvalParams *params, int count, int grid, int layout, bool dense,
+                                   int max_hot, double *partial, double *drift_out, cudaStream_t s);
 
 // prep (eval.cu).  These run while the host is still checking the problem,
 // so they skip columns outside [0, d) and row ranges outside [0, nnz].

@@ -20,6 +20,8 @@
 // float64 atomics at L2; dense problems with few columns, and the most
 // frequent columns of sparse ones, first accumulate per block in shared
 // memory.
+#include <algorithm>
+
 #include "asaga_internal.h"
 #include "device_common.cuh"
 
@@ -254,6 +256,76 @@ __global__ void __launch_bounds__(kEvalBlock) scatter_alpha_rows_kernel(const Ev
     }
 }
 
+// ---- the batched abar recomputation (blockIdx.y = instance)
+
+__global__ void __launch_bounds__(kEvalBlock) batch_zero_acc_kernel(const EvalParams *__restrict__ params) {
+    const EvalParams &e = params[blockIdx.y];
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < e.d; v += (int64_t)gridDim.x * blockDim.x)
+        e.acc[v] = 0.0;
+}
+
+// acc_i[v] += sum_r (alpha_r / n_i) a_rv over instance i's rows, a warp per
+// row; the instance's frequent columns (or all of its dense columns, up to
+// kSmemCols) accumulate per block in shared memory first.
+template <typename T, typename I, bool kDense>
+__global__ void __launch_bounds__(kEvalBlock) batch_scatter_alpha_kernel(const EvalParams *__restrict__ params) {
+    extern __shared__ double sacc[];
+    __shared__ EvalParams sp;
+    if (threadIdx.x == 0) sp = params[blockIdx.y];
+    __syncthreads();
+    if (sp.n <= 0) return;
+    const int nslots = kDense ? (sp.d <= kSmemCols ? (int)sp.d : 0) : (sp.hot_slot ? sp.n_hot : 0);
+    for (int v = threadIdx.x; v < nslots; v += blockDim.x) sacc[v] = 0.0;
+    __syncthreads();
+    const double inv_n = 1.0 / (double)sp.n;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = warp; i < sp.n; i += nwarps) {
+        const double w = (double)__ldg(sp.alpha + i) * inv_n;  // the same in every lane
+        if (w == 0.0) continue;
+        int64_t start;
+        int len;
+        row_range<T, kDense>(sp, i, start, len);
+        for (int k = lane; k < len; k += 32) {
+            const int c = kDense ? k : col_stream<I>(sp.col_idx, start + k);
+            const double contrib = w * (double)value_at<T>(sp.values, i, start + k);
+            const int slot = kDense ? (nslots ? c : -1) : (nslots ? __ldg(sp.hot_slot + c) : -1);
+            if (slot >= 0)
+                atomicAdd(sacc + slot, contrib);
+            else
+                atomicAdd(sp.acc + c, contrib);
+        }
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < nslots; v += blockDim.x)
+        atomicAdd(sp.acc + (kDense ? v : sp.hot_col[v]), sacc[v]);
+}
+
+// abar_v <- (float)acc_v over instance i's columns; partial[i * grid + b] <-
+// the block's max |abar_v(before) - acc_v|.
+__global__ void __launch_bounds__(kEvalBlock) batch_abar_finish_kernel(const EvalParams *__restrict__ params,
+                                                                       double *partial) {
+    const EvalParams &e = params[blockIdx.y];
+    double local = 0.0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < e.d; v += (int64_t)gridDim.x * blockDim.x) {
+        float4 *sv = e.state + v * e.stride;
+        const double exact = e.acc[v];
+        local = fmax(local, fabs((double)sv->y - exact));
+        sv->y = (float)exact;
+    }
+    const double r = block_reduce(local, true);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = r;
+}
+
+__global__ void batch_drift_kernel(const double *partial, int grid, double *drift_out) {
+    const double *p = partial + (int64_t)blockIdx.x * grid;
+    double v = 0.0;
+    for (int j = threadIdx.x; j < grid; j += blockDim.x) v = fmax(v, p[j]);
+    const double r = block_reduce(v, true);
+    if (threadIdx.x == 0) drift_out[blockIdx.x] = r;
+}
+
 __global__ void __launch_bounds__(kEvalBlock) column_finish_kernel(const EvalParams P, int mode, double *acc,
                                                                    double *partial) {
     double local = 0.0;
@@ -437,6 +509,32 @@ cudaError_t launch_batch_objective(const EvalParams *params, int count, int grid
     cudaError_t e = with_layout(layout, dense, BatchObjective{params, count, grid, partial, s}, cudaErrorInvalidValue);
     if (e != cudaSuccess) return e;
     batch_objective_finish_kernel<<<count, 256, 0, s>>>(params, partial, grid, f_out);
+    return cudaGetLastError();
+}
+
+struct BatchScatterAlpha {
+    const EvalParams *params;
+    int count, grid;
+    size_t smem;
+    cudaStream_t s;
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        batch_scatter_alpha_kernel<T, I, kDense><<<dim3(grid, count), kEvalBlock, smem, s>>>(params);
+        return cudaGetLastError();
+    }
+};
+
+cudaError_t launch_batch_recompute(const EvalParams *params, int count, int grid, int layout, bool dense,
+                                   int max_hot, double *partial, double *drift_out, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    batch_zero_acc_kernel<<<dim3(grid, count), kEvalBlock, 0, s>>>(params);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)(dense ? kSmemCols : std::max(0, max_hot)) * sizeof(double);
+    e = with_layout(layout, dense, BatchScatterAlpha{params, count, grid, smem, s}, cudaErrorInvalidValue);
+    if (e != cudaSuccess) return e;
+    batch_abar_finish_kernel<<<dim3(grid, count), kEvalBlock, 0, s>>>(params, partial);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    batch_drift_kernel<<<count, 256, 0, s>>>(partial, grid, drift_out);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,8 @@ At these sizes the oracle cannot follow an asynchronous run update by
 update, so the tests check what it can compute at any size:
   * set-up constants (L, gamma0, Delta, longest row) against the oracle;
   * one epoch replayed in order by a single warp against the serial float64
-    oracle on the same rows: relative l2 <= 1e-4 (as for the small cases);
+    oracle on the same rows: relative l2 <= 1e-4 and per element
+    max_v |x_v - x*_v| <= 1e-3 max_v |x*_v| (as for the small cases);
   * after asynchronous epochs at the tuned schedule: the float64 objective
     and gradient at the GPU iterate against the oracle's (1e-12 / 1e-11),
     and abar recomputed from the memory against the oracle's sum rounded to
@@ -79,9 +80,10 @@ def test_one_epoch_in_order_matches_the_oracle_at_full_size(workload):
         x, abar, alpha = asaga.asaga_get_state(c.ctx)
         gamma = asaga.asaga_get_info(c.ctx)["gamma"]
     st = R.sparse_saga(p, R.State.zeros(p), idx, gamma)
-    assert rel(x, st.x) <= 1e-4, rel(x, st.x)
-    assert rel(alpha, st.alpha) <= 1e-4
-    assert rel(abar, st.abar) <= 1e-4
+    for name, a, b in (("x", x, st.x), ("alpha", alpha, st.alpha), ("abar", abar, st.abar)):
+        assert rel(a, b) <= 1e-4, (name, rel(a, b))
+        # per element, against the largest coordinate (the tolerance of test_gpu_parity)
+        assert np.max(np.abs(a - b)) <= 1e-3 * np.max(np.abs(b)), name
 
 
 def test_tuned_schedule_evaluations_and_target_at_full_size(workload):

@@ -3,7 +3,14 @@
 Tolerances:
   * deterministic replay (one warp, updates in order, float32 state) vs the
     float64 serial Sparse SAGA on the same index sequence: relative l2 error
-    <= 1e-4 on x, alpha and abar after one epoch;
+    <= 1e-4 on x, alpha and abar after one epoch, and per element
+    max_v |x_v - x*_v| <= 1e-3 max_v |x*_v| (likewise for alpha and abar).
+    The l2 bound limits the average error; each coordinate's float32 error is
+    rounding of its sum of updates (about 6e-8 of their size) plus the error
+    of the deltas, which reaches every coordinate in proportion to a_iv, so no
+    coordinate should exceed ~1e-4 of the largest.  Ten times the l2
+    tolerance keeps a margin and still fails a coordinate that is wrong by a
+    sizeable part of itself unless it is below 1e-3 of the largest;
   * float64 evaluations (objective, gradient, abar recomputation) at the
     GPU's float32 iterate widened exactly: relative error <= 1e-12 (sums of
     at most ~1e3 terms per row in a different order give ~1e-14);
@@ -18,6 +25,7 @@ from paper_1606_04809_gb300 import asaga, build, synth
 pytestmark = pytest.mark.gpu
 
 DET_TOL = 1e-4
+ELEM_TOL = 1e-3
 EVAL_TOL = 1e-12
 
 
@@ -34,6 +42,14 @@ def rel(a, b):
     b = np.asarray(b, dtype=np.float64)
     nb = np.linalg.norm(b)
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def elem(a, b):
+    """max_v |a_v - b_v| / max_v |b_v|"""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = np.max(np.abs(b)) if b.size else 0.0
+    return np.max(np.abs(a - b)) / (scale if scale > 0 else 1.0) if b.size else 0.0
 
 
 def quantized(p, storage):
@@ -56,9 +72,9 @@ def replay_pair(p, idx, storage, **opt):
 
 def assert_replay(p, idx, storage, tol=DET_TOL, **opt):
     (x, abar, alpha), st, _ = replay_pair(p, idx, storage, **opt)
-    assert rel(x, st.x) <= tol, rel(x, st.x)
-    assert rel(alpha, st.alpha) <= tol, rel(alpha, st.alpha)
-    assert rel(abar, st.abar) <= tol, rel(abar, st.abar)
+    for name, a, b in (("x", x, st.x), ("alpha", alpha, st.alpha), ("abar", abar, st.abar)):
+        assert rel(a, b) <= tol, (name, rel(a, b))
+        assert elem(a, b) <= 10 * tol, (name, elem(a, b))
     return x, st
 
 
