@@ -19,10 +19,13 @@ float64 checker see the same matrix bit for bit.
 from __future__ import annotations
 
 import concurrent.futures
+import ctypes
 import dataclasses
 import hashlib
 import math
 import os
+import subprocess
+import threading
 from typing import Optional
 
 import numpy as np
@@ -66,9 +69,20 @@ class Problem:
         assert self.dense
         return self.values.reshape(self.n, self.d)
 
+    def values_f64(self) -> np.ndarray:
+        """The values as float64 (bfloat16 bits widened exactly when the problem
+        holds raw bits, meta['values_bits'] == 'bf16')."""
+        if self.values.dtype == np.uint16:
+            return (self.values.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+        return self.values
+
     def fingerprint(self) -> dict:
         """Platform-stable summary used to check that a stored result belongs to
-        the same generated problem: exact integer structure plus value sums."""
+        the same generated problem: exact integer structure plus value sums
+        (for the C generator's problems: the digest of its per-row checksums,
+        which cover lengths, columns, stored values and labels)."""
+        if "row_digest" in self.meta:
+            return {"row_digest": self.meta["row_digest"], "n": self.n, "d": self.d, "nnz": self.nnz}
         h = hashlib.sha256()
         h.update(np.ascontiguousarray(self.row_ptr, dtype="<i8").tobytes())
         h.update(np.ascontiguousarray(self.col_idx, dtype="<i4").tobytes())
@@ -361,3 +375,116 @@ def logistic_batch(count: int = 256, seed: int = 51, n_range=(10_000, 200_000), 
                                    zipf_s=1.1, values="abs_normal", storage=storage, lam=float(lams[k]),
                                    seed=seed * 1000 + k, name=f"batch{seed}_{k}_n{n}_d{d}_{storage}"))
     return out
+
+
+# --------------------------------------------------------------------------
+# the C generator (synth_gen.c) for the full-size batch workload
+# --------------------------------------------------------------------------
+
+_GEN_SRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "synth_gen.c")
+_GEN_LIB = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libsynthgen.so")
+_gen = None
+_gen_lock = threading.Lock()
+
+
+def build_generator(force: bool = False) -> str:
+    """Compiles synth_gen.c with gcc (no fast-math, no contraction: the same
+    bits on x86-64 and aarch64) into _build/libsynthgen.so."""
+    if not force and os.path.exists(_GEN_LIB) and os.path.getmtime(_GEN_LIB) >= os.path.getmtime(_GEN_SRC):
+        return _GEN_LIB
+    os.makedirs(os.path.dirname(_GEN_LIB), exist_ok=True)
+    tmp = _GEN_LIB + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+                    "-pthread", _GEN_SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _GEN_LIB)
+    return _GEN_LIB
+
+
+def _generator():
+    global _gen
+    with _gen_lock:
+        if _gen is None:
+            L = ctypes.CDLL(build_generator())
+            i64, i32, u64, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, ctypes.c_double, ctypes.c_void_p
+            L.synth_gen_rows.argtypes = [u64, i64, i64, dbl, i64, i64, vp, i32]
+            L.synth_gen_rows.restype = i64
+            L.synth_gen_fill.argtypes = [u64, i64, i64, dbl, i64, i64, dbl, i32, vp, vp, vp, vp, vp, vp, i32]
+            L.synth_gen_fill.restype = i32
+            L.synth_gen_log.argtypes = [dbl]
+            L.synth_gen_log.restype = dbl
+            L.synth_gen_exp.argtypes = [dbl]
+            L.synth_gen_exp.restype = dbl
+            _gen = L
+        return _gen
+
+
+def fast_sparse_logistic(n: int, d: int, *, k_mean: float, k_min: int, k_max: int, zipf_s: float = 1.1,
+                         storage: str = "bf16", lam: float, seed: int, name: str = "fast_sparse_logistic",
+                         values: str = "f64", threads: Optional[int] = None) -> Problem:
+    """Sparse l2-logistic problem from the C generator (synth_gen.c):
+    row lengths round(k_mean + sqrt(k_mean) N(0,1)) clipped to [k_min, k_max],
+    Zipf(zipf_s) columns (distinct within a row, through a seeded column
+    permutation), |N(0,1)| values scaled to unit rows on the storage grid
+    (f32 or bf16), labels sign(a.w* + 0.1 eps).  values='f64' keeps float64
+    values; values='bits' keeps bfloat16 bits (uint16, half the host memory
+    of float32; bf16 storage only).  The same bits on every host."""
+    if storage not in ("f32", "bf16") or values not in ("f64", "bits") or (values == "bits" and storage != "bf16"):
+        raise ValueError("storage f32 or bf16; values 'bits' needs bf16 storage")
+    L = _generator()
+    threads = int(threads or min(64, os.cpu_count() or 1))
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    nnz = L.synth_gen_rows(int(seed), n, d, float(k_mean), int(k_min), int(k_max), row_ptr.ctypes.data, threads)
+    if nnz < 0:
+        raise ValueError("bad generator arguments")
+    col = np.empty(nnz, dtype=np.int32)
+    labels = np.empty(n, dtype=np.float64)
+    row_hash = np.empty(n, dtype=np.uint64)
+    v64 = np.empty(nnz, dtype=np.float64) if values == "f64" else None
+    v16 = np.empty(nnz, dtype=np.uint16) if values == "bits" else None
+    rc = L.synth_gen_fill(int(seed), n, d, float(k_mean), int(k_min), int(k_max), float(zipf_s),
+                          1 if storage == "f32" else 2, row_ptr.ctypes.data, col.ctypes.data,
+                          None if v64 is None else v64.ctypes.data, None if v16 is None else v16.ctypes.data,
+                          labels.ctypes.data, row_hash.ctypes.data, threads)
+    if rc != 0:
+        raise RuntimeError("synth_gen_fill failed")
+    digest = hashlib.sha256(row_hash.astype("<u8").tobytes()).hexdigest()
+    return Problem(name=name, n=n, d=d, row_ptr=row_ptr, col_idx=col, values=v64 if v64 is not None else v16,
+                   labels=labels, loss="logistic", lam=float(lam), storage=storage,
+                   meta={"seed": seed, "k_mean": k_mean, "zipf_s": zipf_s, "values": "abs_normal",
+                         "generator": "synth_gen.c", "row_digest": digest,
+                         "values_bits": "bf16" if values == "bits" else None})
+
+
+# The batch workload at its full size: 256 l2-logistic instances with n
+# uniform in [10000, 200000], d uniform in [1000, 50000], density uniform in
+# [0.5%, 2%] (mean row length density * d), Zipf(1.1) columns and lambda on
+# a log grid from 1e-6 to 1e-2 (instance k takes the k-th point), bf16 values.
+FULL_BATCH = dict(count=256, seed=52, n_range=(10_000, 200_000), d_range=(1_000, 50_000),
+                  density_range=(0.005, 0.02), lam_range=(1e-6, 1e-2), storage="bf16")
+
+
+def batch_params(count: int = 256, seed: int = 52, n_range=(10_000, 200_000), d_range=(1_000, 50_000),
+                 density_range=(0.005, 0.02), lam_range=(1e-6, 1e-2), storage: str = "bf16") -> list:
+    """Shapes of the instances of a batch: n, d, mean row length, row length
+    range, lambda and generator seed of each (drawn from a seeded PCG64
+    stream; lambda on the log grid)."""
+    g = _rng(seed, 0)
+    ns = g.integers(n_range[0], n_range[1] + 1, count)
+    ds = g.integers(d_range[0], d_range[1] + 1, count)
+    dens = g.uniform(density_range[0], density_range[1], count)
+    lams = np.logspace(math.log10(lam_range[0]), math.log10(lam_range[1]), count)
+    out = []
+    for k in range(count):
+        n, d = int(ns[k]), int(ds[k])
+        kmean = max(1.0, float(dens[k]) * d)
+        out.append(dict(k=k, n=n, d=d, k_mean=kmean, k_min=1, k_max=max(1, min(d, int(4 * kmean) + 4)),
+                        lam=float(lams[k]), seed=seed * 1000 + k, storage=storage,
+                        name=f"batch{seed}_{k}_n{n}_d{d}_{storage}"))
+    return out
+
+
+def batch_instance(spec: dict, *, values: str = "f64", threads: Optional[int] = None) -> Problem:
+    """One instance of batch_params, generated by the C generator."""
+    return fast_sparse_logistic(spec["n"], spec["d"], k_mean=spec["k_mean"], k_min=spec["k_min"],
+                                k_max=spec["k_max"], zipf_s=1.1, storage=spec["storage"], lam=spec["lam"],
+                                seed=spec["seed"], name=spec["name"], values=values, threads=threads)

@@ -8,6 +8,7 @@ also records the closed-form optimum (normal equations).  The stored
 fingerprint lets a consumer check that it regenerated the same problem.
 
     python tests/golden/make_fstar.py rcv1like covtypelike urllike
+    python tests/golden/make_fstar.py batch256_full      # the full-size batch, all host cores
 """
 from __future__ import annotations
 
@@ -54,10 +55,46 @@ def batch_fstar():
         json.dump(out, f, indent=1)
 
 
+def _full_batch_one(spec):
+    """Certified f* of one full-size batch instance (run in a worker process)."""
+    t0 = time.time()
+    p = synth.batch_instance(spec, values="f64", threads=2)
+    res = R.certified_fstar(p, lambda ep, p=p: synth.sample_indices(p.n, p.n, SAMPLER_SEED, ep),
+                            rel_tol=1e-10, max_epochs=5000, check_every=5)
+    return {"k": spec["k"], "fingerprint": p.fingerprint(), "lambda": p.lam, "fstar": res["fstar"],
+            "bound": res["bound"], "epochs": res["epochs"], "seconds": time.time() - t0}
+
+
+def full_batch_fstar(workers=None):
+    """One certified f* per instance of the full-size batch workload
+    (synth.FULL_BATCH, instances from the C generator), on a pool of worker
+    processes, largest instances first."""
+    import multiprocessing as mp
+    t0 = time.time()
+    specs = synth.batch_params(**synth.FULL_BATCH)
+    order = sorted(specs, key=lambda s: -s["n"] * s["k_mean"])
+    workers = workers or max(1, min(6, (os.cpu_count() or 2) - 1))
+    items = {}
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for r in pool.imap_unordered(_full_batch_one, order):
+            items[r["k"]] = r
+            print(len(items), r["k"], r["fingerprint"]["nnz"], r["lambda"], r["epochs"], f"{r['seconds']:.0f}s",
+                  r["fstar"], flush=True)
+    out = {"name": "batch256_full", "generator": {k: list(v) if isinstance(v, tuple) else v
+                                                  for k, v in synth.FULL_BATCH.items()},
+           "method": "serial float64 Sparse SAGA per instance, certified by |grad f|^2/(2 lambda)",
+           "instances": [items[k] for k in sorted(items)], "seconds": time.time() - t0}
+    with open(os.path.join(HERE, "fstar_batch256_full.json"), "w") as f:
+        json.dump(out, f, indent=1)
+
+
 def main(names):
     for name in names:
         if name == "batch256":
             batch_fstar()
+            continue
+        if name == "batch256_full":
+            full_batch_fstar()
             continue
         t0 = time.time()
         p = WORKLOADS[name]()
