@@ -4,9 +4,11 @@
 One step = one epoch of asynchronous Sparse SAGA updates (n sampled rows,
 Algorithm 2) followed by the segment boundary: the float64 objective and the
 stopping test (plus the float64 abar recomputation every 5th step).  The
-metric is epochs/s on the RCV1-shaped l2-logistic workload (n=700000,
-d=47000, ~75 nnz per row with Zipf(1.1) columns, fp32 values, lambda=1/n,
-gamma=1/(3L)), with the problem resident in HBM.  The line also reports:
+metric is epochs/s, with the problem resident in HBM, on the largest single
+configuration, the URL-shaped l2-logistic workload (C2: n=2.4M, d=3.2M,
+~115 nnz per row with Zipf(1.1) columns, bf16 values, fp32 state,
+lambda=1/n); the RCV1-shaped (C1) and Covtype-shaped (C3) configurations are
+measured the same way in the same run, under other_configs.  For each:
   time_to_target  seconds from x=0 to 1e-6 relative suboptimality against
                   the float64 f* stored in tests/golden;
   e2e             the same epochs/s through the public C ABI from pinned host
@@ -21,8 +23,9 @@ gamma=1/(3L)), with the problem resident in HBM.  The line also reports:
   cpu_baseline    the float64 CPU checker on a bounded sample, one host core;
                   beside it (asaga_all_cores) lock-free ASAGA in C on every
                   host core, the paper's own kind of implementation.
+--workload batch measures the 256-instance batch (C4) instead.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Under torchrun (N > 1) every rank solves its own replica (weak scaling).
 """
 from __future__ import annotations
@@ -44,28 +47,28 @@ import numpy as np  # noqa: E402
 
 from paper_1606_04809_gb300 import synth  # noqa: E402
 
+# L: the smoothness constant of the component the sparse update samples (its
+# l2 part projected and reweighted by D_i, Sec. 4.2); gamma = 1/(3L) is the
+# autotuner's starting step, which it scales by 2^(-k/2)
+L_LOGISTIC = "max_i (0.25 |a_i|^2 + lambda max_{v in S_i} D_v)"
+L_SQUARED = "max_i (|a_i|^2 + lambda max_{v in S_i} D_v)"
 WORKLOADS = {
-    "rcv1like": dict(make=synth.rcv1_like, golden="fstar_rcv1like.json",
-                     desc="l2-logistic, RCV1-shaped synthetic: n=700000, d=47000, ~75 nnz/row (4..1224, "
-                          "lognormal), Zipf(1.1) columns, |N(0,1)| row-normalised, fp32 values, lambda=1/n, "
-                          "gamma=1/(3L)"),
-    "covtypelike": dict(make=synth.covtype_like, golden="fstar_covtypelike.json",
-                        desc="ridge, Covtype-shaped synthetic: n=581000, d=54 dense, N(0,1) standardised, fp16 "
-                             "values, lambda=1e-3, gamma=1/(3L)"),
-    "urllike": dict(make=synth.url_like, golden="fstar_urllike.json",
-                    desc="l2-logistic, URL-shaped synthetic: n=2400000, d=3200000, ~115 nnz/row (16..414), "
-                         "Zipf(1.1) columns, binary row-normalised, bf16 values, lambda=1/n, gamma=1/(3L)"),
+    "rcv1like": dict(make=synth.rcv1_like, golden="fstar_rcv1like.json", L=L_LOGISTIC,
+                     desc="C1, RCV1-shaped l2-logistic: n=700000, d=47000, ~75 nnz/row (4..1224, lognormal), "
+                          "Zipf(1.1) columns, |N(0,1)| row-normalised, fp32 values, lambda=1/n"),
+    "covtypelike": dict(make=synth.covtype_like, golden="fstar_covtypelike.json", L=L_SQUARED,
+                        desc="C3, Covtype-shaped ridge: n=581000, d=54 dense, N(0,1) standardised, fp16 values, "
+                             "lambda=1e-3"),
+    "urllike": dict(make=synth.url_like, golden="fstar_urllike.json", L=L_LOGISTIC,
+                    desc="C2, URL-shaped l2-logistic: n=2400000, d=3200000, ~115 nnz/row (16..414), Zipf(1.1) "
+                         "columns, binary row-normalised, bf16 values, fp32 state, lambda=1/n"),
 }
 ABAR_EVERY = 5
 TARGET = 1e-6
-# 256 independent l2-logistic instances (a regularisation path): the batch workload (n ~ U[10k, 200k],
-# d ~ U[1k, 50k]) with n and d scaled by 1/10 so that the seeded CPU generator and the float64
-# certificates stay within minutes
-BATCH = dict(count=256, seed=51, n_range=(1_000, 20_000), d_range=(100, 5_000), density_range=(0.005, 0.02),
-             lam_range=(1e-6, 1e-2), storage="bf16")
-BATCH_DESC = ("256 l2-logistic instances: n~U[1000,20000], d~U[100,5000], density~U[0.5%,2%], Zipf(1.1) columns, "
-              "|N(0,1)| row-normalised, lambda on a log grid 1e-6..1e-2, bf16 values, fp32 state "
-              "(n and d scaled 1/10 from the specified batch)")
+# the batch workload (C4): 256 independent l2-logistic instances (a regularisation path)
+BATCH_DESC = ("C4, 256 l2-logistic instances: n~U[10000,200000], d~U[1000,50000], density~U[0.5%,2%] "
+              "(rows of about density*d entries), Zipf(1.1) columns, |N(0,1)| row-normalised, lambda on a log "
+              "grid 1e-6..1e-2, bf16 values, fp32 state")
 
 
 def parse():
@@ -74,9 +77,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rcv1like", choices=sorted(WORKLOADS) + ["batch"])
-    ap.add_argument("--single-sample", type=int, default=256,
+    ap.add_argument("--workload", default="urllike", choices=sorted(WORKLOADS) + ["batch"])
+    ap.add_argument("--also", default="rcv1like,covtypelike",
+                    help="other configurations measured in the same line (comma separated, '' for none)")
+    ap.add_argument("--also-steps", type=int, default=100, help="timed steps of each --also configuration")
+    ap.add_argument("--single-sample", type=int, default=32,
                     help="batch workload: instances also solved one at a time in fp32 for comparison")
+    ap.add_argument("--batch-count", type=int, default=0, help="batch workload: the first K instances only")
+    ap.add_argument("--batch-max-epochs", type=float, default=3000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
@@ -169,32 +177,29 @@ def measured_peak_hbm():
     return 6800.0, "fallback"
 
 
-def ncu_summary(workload, profile=None):
-    """Per-launch DRAM bytes and the L2 throughput (% of peak) of the update
-    kernel from the committed ncu summary (profiles/update_kernel_<workload>.md,
-    or profiles/<profile>.md), if it was taken on the current kernel source;
-    None otherwise."""
-    path = os.path.join(ROOT, "profiles", f"{profile or 'update_kernel_' + workload}.md")
+def ncu_summary(profile):
+    """Per-launch DRAM bytes and the L2 / DRAM throughput (% of peak) of a
+    kernel from profiles/<profile>.json (written beside the ncu summary of the
+    same name), if it was taken on the current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", f"{profile}.json")
     src = os.path.join(ROOT, "paper_1606_04809_gb300", "csrc", "update.cu")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    kv = {}
-    for line in open(path):
-        if ":" in line and line.strip().startswith("- "):
-            k, v = line.strip()[2:].split(":", 1)
-            kv[k.strip()] = v.strip().strip("`")
-    if kv.get("update.cu sha256") != sha:
-        return None
     try:
-        out = {"traffic": int(float(kv["traffic_bytes_per_launch"]))}
+        kv = json.load(open(path))
+    except Exception:
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("update_cu_sha256") != sha:
+        return None
+    out = {}
+    try:
+        out["traffic"] = int(kv["traffic_bytes_per_launch"])
     except Exception:
         return None
     for key, name in (("l2_throughput_pct_of_peak", "l2_pct"), ("dram_throughput_pct_of_peak", "dram_pct")):
-        try:
+        if key in kv:
             out[name] = float(kv[key])
-        except Exception:
-            pass
     return out
 
 
@@ -317,7 +322,9 @@ def run_reference(args, p, wl):
 
 
 def run_batch(args):
-    """Batched bf16 solve of many instances vs the same instances solved one at a time in fp32."""
+    """The 256-instance batch (C4) at its specified size: batched bf16 solve
+    of every instance in one persistent, graph-captured launch per segment,
+    against the same instances solved one launch at a time in fp32."""
     import torch
     from paper_1606_04809_gb300 import asaga
     from paper_1606_04809_gb300 import build as lib_build
@@ -330,16 +337,37 @@ def run_batch(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib_build.build()
     asaga.load()
-    ps_all = synth.logistic_batch(**BATCH)
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "fstar_batch256.json")))
-    fs_all = np.array([g["fstar"] for g in gold["instances"]])
-    for p, g in zip(ps_all, gold["instances"]):
-        if p.fingerprint()["structure_sha256"] != g["fingerprint"]["structure_sha256"]:
-            raise SystemExit("regenerated batch differs from the one f* was computed for")
-    mine = sharding.rank_instances([sharding.instance_cost(p) for p in ps_all], world, rank)
-    ps = [ps_all[i] for i in mine]
-    fs = fs_all[mine]
+    phases = {}
+    t_all = time.perf_counter()
+    specs = synth.batch_params(**synth.FULL_BATCH)
+    if args.batch_count:
+        specs = specs[: args.batch_count]
+    gold_path = os.path.join(ROOT, "tests", "golden", "fstar_batch256_full.json")
+    gold = {g["k"]: g for g in json.load(open(gold_path))["instances"]} if os.path.exists(gold_path) else {}
+    mine = sharding.rank_instances([s["n"] * s["k_mean"] for s in specs], world, rank)
     stream = torch.cuda.current_stream()
+    # generate each instance on the host (C generator, all cores), check it is
+    # the problem f* was certified for, move it to the device and drop the host copy
+    t0 = time.perf_counter()
+    metas, structs, fs, keep = [], [], [], []
+    for i in mine:
+        p = synth.batch_instance(specs[i], values="bits")
+        g = gold.get(specs[i]["k"])
+        if g is None or g["fingerprint"] != p.fingerprint():
+            raise SystemExit(f"instance {i}: no certified f* for this generated problem")
+        fs.append(g["fstar"])
+        dev = [torch.from_numpy(p.row_ptr).to("cuda"), torch.from_numpy(p.col_idx).to("cuda"),
+               torch.from_numpy(p.values.view(np.int16)).to("cuda"), torch.from_numpy(p.labels).to("cuda")]
+        keep.append(dev)
+        structs.append(asaga.Problem(p.n, p.d, *dev[:3], "bf16", dev[3], on_device=True, nnz=p.nnz))
+        metas.append(synth.Problem(p.name, p.n, p.d, p.row_ptr[:0], p.col_idx[:0], p.values[:0], p.labels[:0],
+                                   p.loss, p.lam, p.storage, meta={"nnz": p.nnz}))
+        metas[-1].row_ptr = np.array([0, p.nnz])  # nnz only (the arrays live on the device)
+        del p
+    fs = np.array(fs)
+    torch.cuda.synchronize()
+    phases["generate_and_copy_s"] = time.perf_counter() - t0
+    nnz_mine = int(sum(m.nnz for m in metas))
 
     def max_over_ranks(v):
         if world == 1:
@@ -348,11 +376,16 @@ def run_batch(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    b = asaga.Batch(ps, storage="bf16", values_dtype="bf16", epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
+    t0 = time.perf_counter()
+    b = asaga.Batch(metas, storage="bf16", structs=structs, epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
                     cuda_stream=stream.cuda_stream)
+    del structs, keep  # the library holds its own copy
+    torch.cuda.synchronize()
+    phases["create_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     tune = asaga.asaga_batch_autotune(b.b, b.count)
-    tune_s = time.perf_counter() - t0
+    phases["autotune_s"] = time.perf_counter() - t0
+    infos = [asaga.asaga_batch_get_info(b.b, i) for i in range(b.count)]
     for _ in range(args.warmup):
         asaga.asaga_batch_run(b.b, b.count, 1)
     if world > 1:
@@ -371,88 +404,100 @@ def run_batch(args):
     for _ in range(args.steps):
         st, res = asaga.asaga_batch_run(b.b, b.count, 1)
         launches += res[0].kernel_launches
-        seg_s += res[0].solver_seconds  # the batch epoch's segment (one CUDA graph)
+        seg_s += res[0].solver_seconds  # the batch epoch's device time (graph segment and recomputation)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    b.close()
     # HBM roofline of the batch epoch: A's bytes and the per-update row data of
     # every instance over the segment's device time (update launch plus the
     # batched objective, which the segment also holds: a lower bound on the
     # update kernel's own rate)
-    hbm_bytes = sum(update_hbm_bytes(p, "bf16") for p in ps)
+    hbm_bytes = sum(update_hbm_bytes(m, "bf16") for m in metas)
     peak, peak_kind = measured_peak_hbm()
     seg_ms = 1e3 * seg_s / args.steps
     achieved = hbm_bytes / (seg_ms * 1e-3) / 1e9
-    ncu = ncu_summary("batch256", profile="batch_update_kernel_batch256") or {}
+    ncu = ncu_summary("batch_update_kernel_batch256") or {}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu.get("traffic"),
                 "kernel": "batch segment: batch_update_kernel + the batched objective (one CUDA graph per batch epoch)",
                 "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": seg_ms, "peak_source": peak_kind,
                 "l2_throughput_pct_of_peak_ncu": ncu.get("l2_pct"), "dram_throughput_pct_of_peak_ncu": ncu.get("dram_pct")}
-    # time to 1e-6 for every instance of the batch
-    b = asaga.Batch(ps, storage="bf16", values_dtype="bf16", epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
-                    cuda_stream=stream.cuda_stream)
-    asaga.asaga_batch_set_schedule(b.b, warps=[t["warps"] for t in tune], gamma=[t["gamma"] for t in tune])
+    # time to 1e-6 of every instance, from x = 0 with the tuned schedule
+    asaga.asaga_batch_reset(b.b)
     t0 = time.perf_counter()
-    st, res = asaga.asaga_batch_run(b.b, b.count, 5000, TARGET, fs)
+    st, res = asaga.asaga_batch_run(b.b, b.count, args.batch_max_epochs, TARGET, fs)
     batch_wall = time.perf_counter() - t0
     batch_dev = max(r.solver_seconds for r in res)
-    b.close()
     ttt = {"status": asaga.STATUS_NAMES[st], "seconds_device": max_over_ranks(batch_dev), "seconds_wall": batch_wall,
            "max_epochs": max(r.epochs for r in res), "mean_epochs": float(np.mean([r.epochs for r in res])),
-           "worst_rel_subopt": float(max(r.rel_subopt for r in res))}
+           "worst_rel_subopt": float(max(r.rel_subopt for r in res)),
+           "instances_at_target": int(sum(r.rel_subopt <= TARGET for r in res)), "instances": len(res),
+           "per_instance_seconds_device": [r.solver_seconds for r in res],
+           "per_instance_epochs": [r.epochs for r in res]}
+    b.close()
     # the same instances one launch at a time, fp32 (a sample, every k-th instance)
     single = None
     if args.single_sample > 0 and rank == 0:
-        step = max(1, len(ps) // args.single_sample)
-        sample = list(range(0, len(ps), step))[: args.single_sample]
+        step = max(1, len(mine) // args.single_sample)
+        sample = list(range(0, len(mine), step))[: args.single_sample]
         tot_dev = tot_wall = tot_tune = 0.0
         statuses, failed = [], []
-        for i in sample:
-            with asaga.Context(ps[i], storage="f32", seed=i, abar_recompute_every=ABAR_EVERY,
+        for j in sample:
+            p = synth.batch_instance(specs[mine[j]], values="bits")
+            with asaga.Context(p, storage="f32", values_dtype="f32", seed=j, abar_recompute_every=ABAR_EVERY,
                                cuda_stream=stream.cuda_stream) as c:
                 t0 = time.perf_counter()
                 tune1 = asaga.asaga_autotune(c.ctx, 20)
                 tot_tune += time.perf_counter() - t0
-                s1, r1 = asaga.asaga_run(c.ctx, 5000, TARGET, fs[i])
+                s1, r1 = asaga.asaga_run(c.ctx, args.batch_max_epochs, TARGET, fs[j])
                 statuses.append(asaga.STATUS_NAMES[s1])
                 tot_dev += r1.solver_seconds + r1.eval_seconds
                 tot_wall += r1.seconds
                 if s1 != asaga.OK:
-                    failed.append({"instance": i, "n": ps[i].n, "d": ps[i].d, "lambda": ps[i].lam,
+                    failed.append({"instance": mine[j], "n": p.n, "d": p.d, "lambda": p.lam,
                                    "status": asaga.STATUS_NAMES[s1], "epochs": r1.epochs,
-                                   "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"],
-                                   "tune_score": tune1["score"], "tune_trials": tune1["trials"]})
-        batch_sample = float(max(res[i].solver_seconds for i in sample))
+                                   "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"]})
+            del p
+        batch_sample = float(max(res[j].solver_seconds for j in sample))
         single = {"instances": len(sample), "storage": "f32", "sum_seconds_device": tot_dev,
                   "sum_seconds_wall": tot_wall, "autotune_wall_seconds": tot_tune,
                   "all_ok": all(x == "ASAGA_OK" for x in statuses), "failed": failed,
                   "batch_seconds_for_same_instances": batch_sample,
                   "batch_seconds_all_instances": batch_dev,
-                  "speedup_batch_vs_single_same_instances": tot_dev / batch_sample if batch_sample > 0 else None}
-    # CPU baseline: the float64 oracle, three epochs (each with its objective)
-    # on every 4th instance, scaled to the whole batch by nonzeros
+                  "speedup_batch_vs_single_same_instances": tot_dev / batch_sample if batch_sample > 0 else None,
+                  "note": "time to 1e-6 on both sides counts the updates, the float64 evaluations and the abar "
+                          "recomputations (device time)"}
+    # CPU baseline: the float64 oracle, one epoch (with its objective) on a
+    # sample of instances, scaled to the whole batch by nonzeros
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        sample = list(range(0, len(ps), 4))
-        epochs_each, el = 3, 0.0
-        for i in sample:
-            el += time_checker(ps[i], 0.0, steps=epochs_each)[2]
-        nnz_sample = sum(ps[i].nnz for i in sample)
-        per_batch = el / epochs_each * sum(p.nnz for p in ps) / max(1, nnz_sample)
+        sample = list(range(0, len(mine), max(1, len(mine) // 16)))
+        el, nnz_sample = 0.0, 0
+        for j in sample:
+            p = synth.batch_instance(specs[mine[j]], values="f64")
+            el += time_checker(p, 0.0, steps=1)[2]
+            nnz_sample += p.nnz
+            del p
+        per_batch = el * nnz_mine / max(1, nnz_sample)
         cpu = {"value": 1.0 / per_batch, "unit": "epochs/s (whole batch)", "cores": 1, "kind": "oracle",
-               "sample": f"{epochs_each} epochs of serial float64 Sparse SAGA + objective on {len(sample)} of "
-                         f"{len(ps)} instances ({el:.2f} s), scaled to the batch by nonzeros"}
+               "sample": f"1 epoch of serial float64 Sparse SAGA + objective on {len(sample)} of "
+                         f"{len(mine)} instances ({el:.1f} s), scaled to the batch by nonzeros"}
+    phases["total_s"] = time.perf_counter() - t_all
     if rank == 0:
+        paths = {}
+        for inf in infos:
+            key = f"{inf['row_threshold']}/{inf['row_group']}"
+            paths[key] = paths.get(key, 0) + 1
         line = {"metric": "epochs/s", "value": world * args.steps / (ms * 1e-3), "unit": "epochs/s (whole batch)",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 values, f32 state",
-                "data": "synthetic", "config": {"workload": BATCH_DESC, "instances_per_rank": len(ps),
-                                                "nnz_total": int(sum(p.nnz for p in ps_all))},
-                "instance_epochs_per_s": world * args.steps * len(ps) / (ms * 1e-3),
-                "time_to_target": ttt, "autotune_wall_seconds": tune_s, "one_at_a_time_fp32": single,
+                "data": "synthetic", "config": {"workload": BATCH_DESC, "instances_per_rank": len(mine),
+                                                "nnz_per_rank": nnz_mine,
+                                                "row_paths_threshold_over_group": paths,
+                                                "warps_total": int(sum(t["warps"] for t in tune))},
+                "instance_epochs_per_s": world * args.steps * len(mine) / (ms * 1e-3),
+                "time_to_target": ttt, "one_at_a_time_fp32": single, "phases": phases,
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -526,46 +571,21 @@ def run_experiment(args):
     print(json.dumps(out), flush=True)
 
 
-def main():
-    args = parse()
-    if args.experiment:
-        return run_experiment(args)
-    if args.workload == "batch":
-        return run_batch(args)
-    world, rank, local = dist_env()
-    wl = WORKLOADS[args.workload]
-    p = wl["make"]()
-    if args.impl == "reference":
-        return run_reference(args, p, wl)
-
+def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
+    """One configuration at N = world GPUs: autotune, `steps` timed steps, time
+    to 1e-6 from x = 0, end to end through the C ABI, CPU baselines.  Returns
+    the keys of a bench line (without the process-level ones)."""
     import torch
     from paper_1606_04809_gb300 import asaga
-    from paper_1606_04809_gb300 import build as lib_build
 
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    lib_build.build()
-    asaga.load()
-    stream = torch.cuda.current_stream()
+    world, rank, local, stream, barrier, max_over_ranks = env
+    wl = WORKLOADS[name]
+    p = wl["make"]()
     storage = p.storage if p.storage != "f64" else "f32"
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(v):
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
-
     opts = dict(seed=1000 + rank, abar_recompute_every=ABAR_EVERY, cuda_stream=stream.cuda_stream,
                 compact=args.compact)
     ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
-    # schedule: concurrent warps and step size picked by the native autotuner
+    # schedule: warps, step size, block shape and row path picked by the native autotuner
     if args.warps > 0:
         L = asaga.asaga_get_info(ctx.ctx)["L"]
         ctx.close()
@@ -579,7 +599,7 @@ def main():
     info = asaga.asaga_get_info(ctx.ctx)
     opts.update(max_warps=info["warps"], gamma=info["gamma"])
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         asaga.asaga_run(ctx.ctx, 1)
     barrier()
     torch.cuda.synchronize()
@@ -593,7 +613,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     solver_s, launches, f_last = 0.0, 0, None
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         s, r = asaga.asaga_run(ctx.ctx, 1)
         solver_s += r.solver_seconds
         launches += r.kernel_launches
@@ -604,12 +624,12 @@ def main():
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1))
 
-    value = world * args.steps / (ms * 1e-3)
-    upd_ms = 1e3 * solver_s / args.steps
+    value = world * steps / (ms * 1e-3)
+    upd_ms = 1e3 * solver_s / steps
     hbm_bytes = update_hbm_bytes(p, storage, info)
     peak, peak_kind = measured_peak_hbm()
     achieved = hbm_bytes / (upd_ms * 1e-3) / 1e9
-    ncu = ncu_summary(args.workload) or {}
+    ncu = ncu_summary(f"update_kernel_{name}") or {}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": ncu.get("traffic"), "kernel": "update_kernel (one launch = one epoch)",
                 "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": upd_ms, "peak_source": peak_kind,
@@ -624,7 +644,7 @@ def main():
         if golden is None:
             ttt = {"status": "skipped", "reason": why}
         else:
-            # the timed context itself, reset to x = 0 (it keeps the tuned schedule and block shape)
+            # the timed context itself, reset to x = 0 (it keeps the tuned schedule)
             asaga.asaga_set_state(ctx.ctx, np.zeros(p.d, np.float32), np.zeros(p.d, np.float32),
                                   np.zeros(p.n, np.float32), 0)
             f0 = asaga.asaga_objective(ctx.ctx)  # f(0), outside the timed run
@@ -640,7 +660,7 @@ def main():
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
-    if args.e2e_steps > 0:
+    if e2e_steps > 0:
         rp = torch.from_numpy(np.ascontiguousarray(p.row_ptr, dtype=np.int64)).pin_memory() if not p.dense else None
         ci = torch.from_numpy(np.ascontiguousarray(p.col_idx, dtype=np.int32)).pin_memory() if not p.dense else None
         npdt = {"f32": np.float32, "f16": np.float16}
@@ -657,47 +677,100 @@ def main():
         d2h = p.d * 4 + 8
         barrier()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(e2e_steps):
             c = asaga.asaga_create(prob, o)
             asaga.asaga_set_schedule(c, info["warps"], info["gamma"], info["warps_per_block"])
+            asaga.asaga_set_row_path(c, info["row_threshold"], info["row_group"])
             asaga.asaga_run(c, 1)
             asaga.load().asaga_get_state(c, xh.data_ptr(), None, None)
             asaga.asaga_destroy(c)
         el = max_over_ranks(time.perf_counter() - t0)
-        e2e = {"value": world * args.e2e_steps / el, "unit": "epochs/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+        e2e = {"value": world * e2e_steps / el, "unit": "epochs/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                "step": "asaga_create(pinned host CSR) + asaga_run(1 epoch) + asaga_get_state(x) + asaga_destroy"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        eps, done, el = time_checker(p, args.cpu_seconds)
+    if rank == 0 and world == 1 and not args.no_cpu and cpu_seconds > 0:
+        eps, done, el = time_checker(p, cpu_seconds)
         cpu = {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
                "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0 ({el:.1f} s)"}
-        cpu["asaga_all_cores"] = time_cpu_asaga(p, args.cpu_seconds * 2,
-                                                golden["fstar"] if golden else None, TARGET)
+        cpu["asaga_all_cores"] = time_cpu_asaga(p, cpu_seconds * 2, golden["fstar"] if golden else None, TARGET)
 
     a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
+    return {
+        "metric": "epochs/s", "value": value, "unit": "epochs/s", "steps": steps, "warmup": warmup,
+        "ms_per_step": ms / steps,
+        "dtype": {"f32": "f32 values, f32 state", "bf16": "bf16 values, f32 state",
+                  "f16": "f16 values, f32 state"}[storage],
+        "config": {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
+                   "L": wl["L"], "gamma_default": "1/(3L)",
+                   "warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
+                   "gamma_over_gamma0": info["gamma"] * 3.0 * info["L"], "L_value": info["L"],
+                   "row_path": {"threshold": info["row_threshold"], "group": info["row_group"]},
+                   "abar_recompute_every": ABAR_EVERY, "compact": args.compact,
+                   "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"],
+                   "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "time_to_target": ttt,
+        "autotune": tune,
+        "e2e": e2e,
+        "roofline": roofline,
+        "hotline": hotline,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "f_last": f_last,
+    }
+
+
+def main():
+    args = parse()
+    if args.experiment:
+        return run_experiment(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        wl = WORKLOADS[args.workload]
+        return run_reference(args, wl["make"](), wl)
+
+    import torch
+    from paper_1606_04809_gb300 import asaga
+    from paper_1606_04809_gb300 import build as lib_build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib_build.build()
+    asaga.load()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    env = (world, rank, local, stream, barrier, max_over_ranks)
+    head = measure(args, args.workload, args.steps, args.warmup, args.e2e_steps, args.cpu_seconds, env)
+    # the other single-instance configurations, each with its own line of keys
+    others = {}
+    for name in [w for w in args.also.split(",") if w and w != args.workload]:
+        others[name] = measure(args, name, min(args.steps, args.also_steps), args.warmup, min(1, args.e2e_steps),
+                               args.cpu_seconds / 2, env)
     if rank == 0:
-        line = {
-            "metric": "epochs/s", "value": value, "unit": "epochs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
-                       "warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
-                       "abar_recompute_every": ABAR_EVERY, "compact": args.compact,
-                       "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"],
-                       "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "time_to_target": ttt,
-            "autotune": tune,
-            "e2e": e2e,
-            "roofline": roofline,
-            "hotline": hotline,
-            "cpu_baseline": cpu,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "f_last": f_last,
-        }
+        line = {"metric": head.pop("metric"), "value": head.pop("value"), "unit": head.pop("unit"),
+                "n_gpus": world, "steps": head.pop("steps"), "warmup": head.pop("warmup"),
+                "ms_per_step": head.pop("ms_per_step"), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": head.pop("dtype"), "data": "synthetic"}
+        line.update(head)
+        line["other_configs"] = others
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

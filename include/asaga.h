@@ -320,6 +320,19 @@ typedef struct {
  * than 2 updates, out NULL. */
 asaga_status asaga_measure_overlap(asaga_ctx *ctx, double epochs, asaga_overlap *out);
 
+/* As asaga_measure_overlap, and also copies the raw trace to times (host
+ * memory, at least 2 x updates values): times[2t] and times[2t + 1] are the
+ * %globaltimer values (ns) just before update t's reads and just after its
+ * writes were issued, t = 0 .. updates - 1 in the launch's update order.
+ * The estimates follow from it: overlap(t) = #{r != t : times[2r] <=
+ * times[2t+1] and times[2r+1] >= times[2t]}; tau_mean its mean, tau_max
+ * its maximum; tau_paper the largest mean over consecutive windows of 100
+ * updates in start order (ties in update order), a trailing partial window
+ * left out; window_ns_mean the mean of times[2t+1] - times[2t].  EINVAL as
+ * asaga_measure_overlap, or capacity < 2 x updates with times not NULL. */
+asaga_status asaga_measure_overlap_trace(asaga_ctx *ctx, double epochs, asaga_overlap *out, uint64_t *times,
+                                         int64_t capacity);
+
 /* Service time of one column's state line under the update's access
  * pattern: the 16-byte read of {x^_v, abar_v, D_v} and then the 2-wide float
  * reduction into x_v and abar_v that depends on it (Algorithm 2's read of x^

@@ -398,3 +398,32 @@ def certified_fstar(p, index_stream, *, gamma: Optional[float] = None, rel_tol: 
             if b <= rel_tol * abs(f):
                 return {"fstar": f, "bound": b, "epochs": ep, "x": st.x.copy()}
     raise RuntimeError("f* not certified within max_epochs")
+
+
+def overlap_estimates(times: np.ndarray) -> dict:
+    """The overlap tau of Assumption 1 estimated from a run's trace as App. E.2
+    does, written out plainly (O(count^2) comparisons: small traces only).
+
+    times[2t], times[2t+1]: when update t started (before its reads) and
+    ended (after its writes).  Iterations r and t overlap when at some point
+    they are processed concurrently, i.e. their closed intervals intersect;
+    overlap(t) counts the other updates that do.  App. E.2 averages the
+    overlap over 100 iterations (here: consecutive windows of 100 updates in
+    start order, ties in update order, a trailing partial window dropped) and
+    takes the largest such average; tau_mean and tau_max are the plain mean
+    and maximum over all updates."""
+    t = np.asarray(times, dtype=np.uint64).reshape(-1, 2)
+    start, end = t[:, 0], t[:, 1]
+    count = start.size
+    ov = np.empty(count, dtype=np.int64)
+    for u in range(count):
+        hits = (start <= end[u]) & (end >= start[u])
+        ov[u] = int(np.count_nonzero(hits)) - 1  # not itself
+    order = np.lexsort((np.arange(count), start))
+    ov_sorted = ov[order]
+    paper = 0.0
+    for w in range(count // 100):
+        paper = max(paper, float(np.sum(ov_sorted[100 * w:100 * (w + 1)])) / 100.0)
+    return {"updates": count, "tau_mean": float(np.sum(ov)) / count, "tau_max": float(np.max(ov)),
+            "tau_paper": paper, "window_ns_mean": float(np.mean((end - start).astype(np.float64))),
+            "overlaps": ov}

@@ -119,6 +119,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_run_indices.argtypes = [vp, vp, i64, i32]
     L.asaga_autotune.argtypes = [vp, dbl, P(asaga_tune_result)]
     L.asaga_measure_overlap.argtypes = [vp, dbl, P(asaga_overlap)]
+    L.asaga_measure_overlap_trace.argtypes = [vp, dbl, P(asaga_overlap), vp, i64]
+    L.asaga_measure_overlap_trace.restype = i32
     L.asaga_objective.argtypes = [vp, P(dbl)]
     L.asaga_full_grad.argtypes = [vp, vp, P(dbl)]
     L.asaga_recompute_abar.argtypes = [vp, P(dbl)]
@@ -277,6 +279,14 @@ def asaga_set_row_path(ctx: int, threshold: int, group: int) -> None:
 def asaga_cancel(ctx: int) -> None:
     """Asks the asaga_run in progress on ctx (in another thread) to stop."""
     _check(ctx, load().asaga_cancel(ctx))
+
+
+def asaga_measure_overlap_trace(ctx: int, epochs: float, count: int):
+    """(estimates, times): times[2t], times[2t+1] = start and end (ns) of update t."""
+    o = asaga_overlap()
+    times = np.zeros(2 * count, dtype=np.uint64)
+    _check(ctx, load().asaga_measure_overlap_trace(ctx, float(epochs), ctypes.byref(o), _ptr(times), times.size))
+    return o.as_dict(), times
 
 
 def asaga_measure_overlap(ctx: int, epochs: float = 1.0) -> dict:

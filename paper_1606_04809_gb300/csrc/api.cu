@@ -1471,12 +1471,16 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
 // interval (reads issued .. writes issued) intersects its own; tau_paper =
 // max over consecutive windows of 100 updates (in start order) of the
 // window's average overlap.
-asaga_status overlap_impl(asaga_ctx *c, double epochs, asaga_overlap *out, std::string *err) {
+asaga_status overlap_impl(asaga_ctx *c, double epochs, asaga_overlap *out, uint64_t *times, int64_t capacity,
+                          std::string *err) {
     if (!out) return fail(err, ASAGA_EINVAL, "out is NULL");
     if (!(epochs > 0) || !std::isfinite(epochs)) return fail(err, ASAGA_EINVAL, "epochs must be > 0");
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const int64_t count = (int64_t)std::llround(epochs * (double)c->n);
     if (count < 2) return fail(err, ASAGA_EINVAL, "need at least 2 updates");
+    if (times && capacity < 2 * count)
+        return fail(err, ASAGA_EINVAL, "times holds " + std::to_string(capacity) + " values, the trace " +
+                                           std::to_string(2 * count));
     uint64_t *trace = nullptr;
     CK(cudaMallocAsync((void **)&trace, 2 * count * sizeof(uint64_t), c->stream), "alloc trace");
     UpdateParams u = update_params(c);
@@ -1507,7 +1511,9 @@ asaga_status overlap_impl(asaga_ctx *c, double epochs, asaga_overlap *out, std::
         order[t] = t;
         window_sum += (double)(ends[t] - starts[t]);
     }
-    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return starts[a] < starts[b]; });
+    if (times) std::copy(h.begin(), h.end(), times);
+    // start order; updates that start at the same time stay in update order
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return starts[a] < starts[b]; });
     std::vector<uint64_t> s_sorted(starts), e_sorted(ends);
     std::sort(s_sorted.begin(), s_sorted.end());
     std::sort(e_sorted.begin(), e_sorted.end());
@@ -2278,7 +2284,13 @@ asaga_status asaga_sample_rows(uint64_t seed, int64_t n, int sampling, uint64_t 
 
 asaga_status asaga_measure_overlap(asaga_ctx *c, double epochs, asaga_overlap *out) {
     if (!c) return ASAGA_EINVAL;
-    return overlap_impl(c, epochs, out, &c->err);
+    return overlap_impl(c, epochs, out, nullptr, 0, &c->err);
+}
+
+asaga_status asaga_measure_overlap_trace(asaga_ctx *c, double epochs, asaga_overlap *out, uint64_t *times,
+                                         int64_t capacity) {
+    if (!c) return ASAGA_EINVAL;
+    return overlap_impl(c, epochs, out, times, capacity, &c->err);
 }
 
 asaga_status asaga_run_indices(asaga_ctx *c, const int64_t *idx, int64_t count, int idx_on_device) {

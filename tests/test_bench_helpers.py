@@ -2,6 +2,7 @@
 behind roofline.achieved, the committed ncu summaries behind roofline.traffic,
 and the bounded-sample arithmetic of the CPU reference arm."""
 import hashlib
+import json
 import os
 
 import numpy as np
@@ -29,30 +30,34 @@ def test_dense_rows_have_no_indices_and_no_row_ptr():
 
 
 def test_a_profile_counts_only_for_the_kernel_source_it_was_captured_on(tmp_path, monkeypatch):
-    """roofline.traffic comes from a committed ncu summary only while update.cu
-    is the source it records; after any change the bench reports null."""
+    """roofline.traffic comes from the machine-readable file beside a committed
+    ncu summary only while update.cu is the source it records; after any
+    change the bench reports null."""
     csrc = tmp_path / "paper_1606_04809_gb300" / "csrc"
     csrc.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
     src = csrc / "update.cu"
     src.write_text("// kernel v1\n")
     sha = hashlib.sha256(src.read_bytes()).hexdigest()
-    (tmp_path / "profiles" / "update_kernel_toy.md").write_text(
-        f"# toy\n\n- update.cu sha256: `{sha}`\n- traffic_bytes_per_launch: `123456`\n"
-        "- l2_throughput_pct_of_peak: `11.5`\n- dram_throughput_pct_of_peak: `1.5`\n")
+    (tmp_path / "profiles" / "update_kernel_toy.json").write_text(json.dumps(
+        {"update_cu_sha256": sha, "traffic_bytes_per_launch": 123456, "l2_throughput_pct_of_peak": 11.5,
+         "dram_throughput_pct_of_peak": 1.5}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    s = bench.ncu_summary("toy")
+    s = bench.ncu_summary("update_kernel_toy")
     assert s == {"traffic": 123456, "l2_pct": 11.5, "dram_pct": 1.5}
-    assert bench.ncu_summary("toy", profile="update_kernel_toy") == s
     src.write_text("// kernel v2\n")
-    assert bench.ncu_summary("toy") is None
+    assert bench.ncu_summary("update_kernel_toy") is None
     assert bench.ncu_summary("missing") is None
 
 
-def test_committed_profiles_parse():
+def test_committed_profiles_have_a_readable_figure_file():
+    """Every ncu summary the bench reads has its figures in a JSON file beside
+    it; the Markdown stays prose and gives the command."""
     for name in ("update_kernel_rcv1like", "update_kernel_urllike", "batch_update_kernel_batch256"):
         text = open(os.path.join(ROOT, "profiles", name + ".md")).read()
-        assert "update.cu sha256" in text and "traffic_bytes_per_launch" in text and "ncu " in text
+        assert "ncu " in text
+        kv = json.load(open(os.path.join(ROOT, "profiles", name + ".json")))
+        assert len(kv["update_cu_sha256"]) == 64 and int(kv["traffic_bytes_per_launch"]) > 0
 
 
 def test_reference_steps_are_bounded_samples_reported_in_epochs():

@@ -95,3 +95,25 @@ def test_batch_cancel_from_another_thread():
         assert s == asaga.ECANCELLED and all(0 < r.epochs < 1e6 for r in res)
         s2, res2 = asaga.asaga_batch_run(b.b, b.count, 2)
         assert s2 == asaga.OK and all(np.isfinite(r.f_last) for r in res2)
+
+
+def test_batched_abar_recomputation_matches_the_checker():
+    """Every 2nd segment recomputes abar = (1/n) sum_i alpha_i a_i of every
+    instance in one batched float64 pass inside the segment's graph; each
+    instance's abar then equals the checker's float64 sum rounded to float32
+    (one ulp: the float64 column sums add atomics in no fixed order)."""
+    ps = small_batch("f32", count=5, seed=65)
+    with asaga.Batch(ps, storage="f32", epochs_per_segment=1, abar_recompute_every=2) as b:
+        s, res = asaga.asaga_batch_run(b.b, b.count, 2)
+        assert s == asaga.OK
+        for i, p in enumerate(ps):
+            _, abar, alpha = asaga.asaga_batch_get_state(b.b, i, p.d, p.n)
+            exact = R.abar_from_scratch(p, alpha.astype(np.float64))
+            np.testing.assert_array_max_ulp(abar, exact.astype(np.float32), maxulp=1)
+            assert 0 < res[i].abar_drift < 1e-4
+        # the cadence counts over the batch's life: the next call's first segment does not recompute
+        s, res = asaga.asaga_batch_run(b.b, b.count, 1)
+        assert s == asaga.OK and all(r.abar_drift == 0 for r in res)
+        asaga.asaga_batch_reset(b.b)
+        x, abar, alpha = asaga.asaga_batch_get_state(b.b, 0, ps[0].d, ps[0].n)
+        assert not x.any() and not abar.any() and not alpha.any()

@@ -491,3 +491,43 @@ def test_quantisation_moves_the_optimum_by_a_reported_amount(values, storage):
     drift = abs(fq - f64) / abs(f64)
     print(f"{values} {storage}: f*(float64 A) = {f64:.12f}, f*(stored A) = {fq:.12f}, relative gap {drift:.2e}")
     assert 0 < drift < 1e-3
+
+
+# ---------------------------------------------------------------- overlap estimator (App. E.2)
+
+def _trace(intervals):
+    return np.array([v for iv in intervals for v in iv], dtype=np.uint64)
+
+
+def test_overlap_of_identical_and_of_disjoint_intervals():
+    """p updates processed at the same time overlap p - 1 others each; updates
+    one after the other overlap none."""
+    est = R.overlap_estimates(_trace([(5, 9)] * 150))
+    assert est["tau_mean"] == 149 and est["tau_max"] == 149 and est["tau_paper"] == 149
+    est = R.overlap_estimates(_trace([(10 * k, 10 * k + 9) for k in range(250)]))
+    assert est["tau_mean"] == 0 and est["tau_max"] == 0 and est["tau_paper"] == 0
+    assert est["window_ns_mean"] == 9
+
+
+def test_overlap_of_a_staircase_has_its_closed_form():
+    """Update k runs over [k, k + w] (closed): it overlaps the updates r with
+    |k - r| <= w, i.e. min(k, w) + min(N - 1 - k, w) others."""
+    N, w = 1000, 37
+    est = R.overlap_estimates(_trace([(k, k + w) for k in range(N)]))
+    want = np.array([min(k, w) + min(N - 1 - k, w) for k in range(N)])
+    assert np.array_equal(est["overlaps"], want)
+    assert est["tau_mean"] == want.sum() / N and est["tau_max"] == 2 * w
+    # windows of 100 in start order: the interior windows see 2w each
+    assert est["tau_paper"] == 2 * w
+
+
+def test_overlap_windows_follow_start_order_and_drop_a_partial_window():
+    """Window averages are taken over consecutive updates in start order, not
+    in update order; the last, partial window is left out."""
+    busy = [(0, 100)] * 100                      # 100 updates at once: 99 each
+    idle = [(200 + 10 * k, 205 + 10 * k) for k in range(100)]  # one after another: 0 each
+    tail = [(10_000, 10_001)] * 50               # a partial window of 49s
+    est = R.overlap_estimates(_trace(idle + tail + busy))  # listed out of start order
+    assert est["tau_paper"] == 99.0
+    est = R.overlap_estimates(_trace(idle + tail))
+    assert est["tau_paper"] == 0.0 and est["tau_max"] == 49
