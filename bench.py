@@ -79,12 +79,13 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="urllike", choices=sorted(WORKLOADS) + ["batch"])
     ap.add_argument("--also", default="rcv1like,covtypelike",
-                    help="other configurations measured in the same line (comma separated, '' for none)")
+                    help="other configurations measured in the same line (comma separated, 'none' for none)")
     ap.add_argument("--also-steps", type=int, default=100, help="timed steps of each --also configuration")
     ap.add_argument("--single-sample", type=int, default=32,
                     help="batch workload: instances also solved one at a time in fp32 for comparison")
     ap.add_argument("--batch-count", type=int, default=0, help="batch workload: the first K instances only")
     ap.add_argument("--batch-max-epochs", type=float, default=3000)
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: keep the default schedule and steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target run")
@@ -206,7 +207,7 @@ def ncu_summary(profile):
 def line_floor(p, kernel_ms):
     """The epoch floor set by the most frequent column's state line.
 
-    Each update whose row holds a column reads that column's 16-byte state and
+    Each update whose row holds a column reads that column's 8-byte state and
     then reduces into it; the line's L2 slice serialises the pairs, so an
     epoch needs at least (rows holding the most frequent column) x (service
     time per pair), the latter measured by asaga_probe_line_rate with enough
@@ -368,6 +369,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     phases["generate_and_copy_s"] = time.perf_counter() - t0
     nnz_mine = int(sum(m.nnz for m in metas))
+    print(f"batch: {len(mine)} instances, {nnz_mine} nonzeros generated in {phases['generate_and_copy_s']:.1f} s",
+          file=sys.stderr, flush=True)
 
     def max_over_ranks(v):
         if world == 1:
@@ -382,9 +385,14 @@ def run_batch(args):
     del structs, keep  # the library holds its own copy
     torch.cuda.synchronize()
     phases["create_s"] = time.perf_counter() - t0
+    print(f"batch: created in {phases['create_s']:.1f} s", file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    tune = asaga.asaga_batch_autotune(b.b, b.count)
+    if args.no_tune:  # the default schedule and steps (for profiling the kernels)
+        tune = [{"warps": asaga.asaga_batch_get_info(b.b, i)["warps"]} for i in range(b.count)]
+    else:
+        tune = asaga.asaga_batch_autotune(b.b, b.count)
     phases["autotune_s"] = time.perf_counter() - t0
+    print(f"batch: tuned in {phases['autotune_s']:.1f} s", file=sys.stderr, flush=True)
     infos = [asaga.asaga_batch_get_info(b.b, i) for i in range(b.count)]
     for _ in range(args.warmup):
         asaga.asaga_batch_run(b.b, b.count, 1)
@@ -429,6 +437,8 @@ def run_batch(args):
     st, res = asaga.asaga_batch_run(b.b, b.count, args.batch_max_epochs, TARGET, fs)
     batch_wall = time.perf_counter() - t0
     batch_dev = max(r.solver_seconds for r in res)
+    print(f"batch: time to target {batch_dev:.2f} s device, {batch_wall:.1f} s wall, "
+          f"{asaga.STATUS_NAMES[st]}", file=sys.stderr, flush=True)
     ttt = {"status": asaga.STATUS_NAMES[st], "seconds_device": max_over_ranks(batch_dev), "seconds_wall": batch_wall,
            "max_epochs": max(r.epochs for r in res), "mean_epochs": float(np.mean([r.epochs for r in res])),
            "worst_rel_subopt": float(max(r.rel_subopt for r in res)),
@@ -442,9 +452,11 @@ def run_batch(args):
         step = max(1, len(mine) // args.single_sample)
         sample = list(range(0, len(mine), step))[: args.single_sample]
         tot_dev = tot_wall = tot_tune = 0.0
+        nnz_sample = 0
         statuses, failed = [], []
         for j in sample:
             p = synth.batch_instance(specs[mine[j]], values="bits")
+            nnz_sample += p.nnz
             with asaga.Context(p, storage="f32", values_dtype="f32", seed=j, abar_recompute_every=ABAR_EVERY,
                                cuda_stream=stream.cuda_stream) as c:
                 t0 = time.perf_counter()
@@ -459,15 +471,18 @@ def run_batch(args):
                                    "status": asaga.STATUS_NAMES[s1], "epochs": r1.epochs,
                                    "rel_subopt": r1.rel_subopt, "warps": tune1["warps"], "gamma": tune1["gamma"]})
             del p
-        batch_sample = float(max(res[j].solver_seconds for j in sample))
+        # one at a time, the instances' times add up; the batch solves all of them in batch_dev
+        all_est = tot_dev if len(sample) == len(mine) else tot_dev * nnz_mine / max(1, nnz_sample)
         single = {"instances": len(sample), "storage": "f32", "sum_seconds_device": tot_dev,
                   "sum_seconds_wall": tot_wall, "autotune_wall_seconds": tot_tune,
                   "all_ok": all(x == "ASAGA_OK" for x in statuses), "failed": failed,
-                  "batch_seconds_for_same_instances": batch_sample,
+                  "sum_seconds_device_all_instances": all_est,
+                  "all_instances": "measured" if len(sample) == len(mine) else
+                                   f"the sample's sum scaled by nonzeros ({nnz_mine} / {nnz_sample})",
                   "batch_seconds_all_instances": batch_dev,
-                  "speedup_batch_vs_single_same_instances": tot_dev / batch_sample if batch_sample > 0 else None,
+                  "speedup_batch_vs_one_at_a_time": all_est / batch_dev if batch_dev > 0 else None,
                   "note": "time to 1e-6 on both sides counts the updates, the float64 evaluations and the abar "
-                          "recomputations (device time)"}
+                          "recomputations (device time); tuning is reported separately"}
     # CPU baseline: the float64 oracle, one epoch (with its objective) on a
     # sample of instances, scaled to the whole batch by nonzeros
     cpu = None
@@ -761,7 +776,7 @@ def main():
     head = measure(args, args.workload, args.steps, args.warmup, args.e2e_steps, args.cpu_seconds, env)
     # the other single-instance configurations, each with its own line of keys
     others = {}
-    for name in [w for w in args.also.split(",") if w and w != args.workload]:
+    for name in [w for w in args.also.split(",") if w and w not in (args.workload, "none")]:
         others[name] = measure(args, name, min(args.steps, args.also_steps), args.warmup, min(1, args.e2e_steps),
                                args.cpu_seconds / 2, env)
     if rank == 0:

@@ -104,9 +104,10 @@ typedef struct {
  *   timeout_s            wall-clock limit of one asaga_run (0 = none).
  *   cuda_stream          cudaStream_t to run on; NULL = a stream the library
  *                        creates.  All work of a context is ordered on it.
- *   column_stride        spacing of the per-column state in 16-byte units
- *                        (1 = packed; 8 = one 128-byte line per column, which
- *                        spreads atomics on very small d); 0 = automatic.
+ *   column_stride        spacing of the per-column state {x_v, abar_v} in
+ *                        8-byte units (1 = packed; 16 = one 128-byte line per
+ *                        column, which spreads atomics on very small d);
+ *                        0 = automatic (16 when d <= 1024, else 1).
  *   plain_writes         1 = replace the atomic adds by non-thread-safe
  *                        load-add-store updates, which lose concurrent adds:
  *                        the comparison of App. G.2 ("Necessity of
@@ -166,7 +167,7 @@ typedef struct {
     double gamma;        /* step size in use                                    */
     double delta;        /* max_v |{i : v in S_i}| / n (Sec. 3.4, "Sparsity")   */
     int warps;           /* concurrent solver warps of asaga_run                */
-    int column_stride;   /* per-column state spacing in 16-byte units           */
+    int column_stride;   /* per-column state spacing in 8-byte units            */
     int64_t device_bytes;/* device memory held by the context                   */
     int64_t max_row_len; /* longest row                                          */
     int n_hot;           /* frequent columns accumulated in shared memory by the
@@ -334,7 +335,7 @@ asaga_status asaga_measure_overlap_trace(asaga_ctx *ctx, double epochs, asaga_ov
                                          int64_t capacity);
 
 /* Service time of one column's state line under the update's access
- * pattern: the 16-byte read of {x^_v, abar_v, D_v} and then the 2-wide float
+ * pattern: the 8-byte read of {x^_v, abar_v} and then the 2-wide float
  * reduction into x_v and abar_v that depends on it (Algorithm 2's read of x^
  * and write of x and abar, for one column v).  `warps` warps each repeat the
  * pair `pairs` times on one line; *ns_per_pair = elapsed device time /
@@ -487,9 +488,13 @@ asaga_status asaga_batch_cancel(asaga_batch *b);
  * warps in proportion to each instance's predicted work (epochs x epoch
  * cost, within the same caps); the second is kept, except that an
  * instance predicted under the first but not under the second keeps its
- * first step at no more warps than the first schedule gave it.  Leaves
- * every instance at x = 0.  results[i] may be NULL; its score is
- * 1 / predicted epochs. */
+ * first step at no more warps than the first schedule gave it.  Last, the
+ * row paths (asaga_batch_set_row_paths) at the tuned warps and steps: every
+ * row of instance i on cores of G_i = min(4, 2^floor(log2(k_i / E))) warps
+ * (k_i its mean row length), for E = 512 and 256 entries per warp, against
+ * single warps, each schedule's batch epoch timed (the faster of two after
+ * one untimed) and the fastest kept if 3% faster.  Leaves every instance at
+ * x = 0.  results[i] may be NULL; its score is 1 / predicted epochs. */
 asaga_status asaga_batch_autotune(asaga_batch *b, double trial_epochs, asaga_tune_result *results);
 
 /* Overrides the schedule: warps[i] (rounded up to a multiple of 4) and/or

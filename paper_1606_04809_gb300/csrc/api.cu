@@ -70,7 +70,8 @@ struct asaga_ctx {
     float *lab32 = nullptr;
     double *lab64 = nullptr;
     float *alpha = nullptr;
-    float4 *state = nullptr;
+    float2 *state = nullptr;      // {x_v, abar_v}, stride float2s apart
+    float *dcol = nullptr;        // D_v
     double *acc64 = nullptr;
     double *partial = nullptr;
     double *dout = nullptr;  // [0] f, [1..] small results
@@ -433,6 +434,7 @@ EvalParams eval_params(const asaga_ctx *c) {
     e.labels = c->lab64;
     e.alpha = c->alpha;
     e.state = c->state;
+    e.dcol = c->dcol;
     e.stride = c->stride;
     e.loss = c->loss;
     e.lambda = c->lambda;
@@ -573,7 +575,7 @@ asaga_status create_buffers(asaga_ctx *c, const asaga_problem *p, const asaga_op
     c->epochs_per_segment = o->epochs_per_segment > 0 ? o->epochs_per_segment : 1;
     c->abar_every = o->abar_recompute_every;
     c->timeout_s = o->timeout_s;
-    c->stride = o->column_stride > 0 ? o->column_stride : (c->d <= 1024 ? 8 : 1);
+    c->stride = o->column_stride > 0 ? o->column_stride : (c->d <= 1024 ? 16 : 1);  // 16 float2s = 128 bytes
 
     const size_t vsz_in = dtype_size(p->values_dtype);
     const size_t vsz = c->vtype == kF32 ? 4 : 2;
@@ -621,7 +623,9 @@ asaga_status create_buffers(asaga_ctx *c, const asaga_problem *p, const asaga_op
     TRY(dev_alloc(&c->alpha, c->n, c, err, "alloc alpha"));
     CK(cudaMemsetAsync(c->alpha, 0, c->n * sizeof(float), c->stream), "memset alpha");
     TRY(dev_alloc(&c->state, (size_t)c->d * c->stride, c, err, "alloc state"));
-    CK(cudaMemsetAsync(c->state, 0, (size_t)c->d * c->stride * sizeof(float4), c->stream), "memset state");
+    CK(cudaMemsetAsync(c->state, 0, (size_t)c->d * c->stride * sizeof(float2), c->stream), "memset state");
+    TRY(dev_alloc(&c->dcol, (size_t)c->d, c, err, "alloc D"));
+    CK(cudaMemsetAsync(c->dcol, 0, (size_t)c->d * sizeof(float), c->stream), "memset D");
     TRY(dev_alloc(&c->acc64, c->d, c, err, "alloc scratch"));
     c->eval_grid = c->sms * 4;
     if (c->eval_grid > kMaxPartials) c->eval_grid = kMaxPartials;
@@ -650,7 +654,7 @@ asaga_status create_setup(asaga_ctx *c, const asaga_options *o, std::string *err
         CK(launch_count_columns(c->col_idx, c->nnz, c->d, count, c->stream), "count kernel");
         ++c->launches;
     }
-    CK(launch_init_state(c->state, c->stride, c->d, count, c->n, c->stream), "init state");
+    CK(launch_init_state(c->state, c->dcol, c->stride, c->d, count, c->n, c->stream), "init state");
     ++c->launches;
     if (count) {
         count_h.resize(c->d);
@@ -755,6 +759,7 @@ void release(asaga_ctx *c) {
     cudaFree(c->lab64);
     cudaFree(c->alpha);
     cudaFree(c->state);
+    cudaFree(c->dcol);
     cudaFree(c->acc64);
     cudaFree(c->partial);
     cudaFree(c->dout);
@@ -787,6 +792,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.labels = c->lab32;
     u.alpha = c->alpha;
     u.state = c->state;
+    u.dcol = c->dcol;
     u.stride = c->stride;
     u.loss = c->loss;
     u.gamma = (float)c->gamma;
@@ -1051,7 +1057,7 @@ asaga_status run_impl(asaga_ctx *c, double max_epochs, double target, double f_s
 
 asaga_status reset_state(asaga_ctx *c, std::string *err) {
     CK(cudaMemsetAsync(c->alpha, 0, c->n * sizeof(float), c->stream), "memset alpha");
-    CK(cudaMemset2DAsync(c->state, (size_t)c->stride * sizeof(float4), 0, 2 * sizeof(float), c->d, c->stream),
+    CK(cudaMemset2DAsync(c->state, (size_t)c->stride * sizeof(float2), 0, sizeof(float2), c->d, c->stream),
        "memset state");
     c->updates_done = 0;
     c->segments_done = 0;
@@ -2118,12 +2124,69 @@ asaga_status batch_refine_predictions(asaga_batch *b, int E, const std::vector<i
     return ASAGA_OK;
 }
 
+// Device time of one batch epoch under the current schedule and steps (the
+// faster of two epochs after one untimed, every instance from x = 0).
+asaga_status batch_time_epoch(asaga_batch *b, double *ms_out, double *seconds, std::string *err) {
+    for (auto *c : b->ctx) TRY(reset_state(c, err));
+    double best = INFINITY;
+    for (int e = 0; e < 3; ++e) {
+        for (int i = 0; i < b->count; ++i) {
+            asaga_ctx *c = b->ctx[i];
+            b->h_up[i].gamma = (float)c->gamma;
+            b->h_up[i].t_begin = (uint64_t)c->updates_done;
+            b->h_up[i].count = c->n;
+        }
+        float ms = 0;
+        TRY(batch_segment(b, false, &ms, err));
+        *seconds += ms * 1e-3;
+        for (auto *c : b->ctx) c->updates_done += c->n;
+        if (e > 0) best = std::min(best, (double)ms);
+    }
+    *ms_out = best;
+    return ASAGA_OK;
+}
+
+asaga_status batch_tune_row_paths(asaga_batch *b, double *seconds, std::string *err) {
+    auto apply = [&](double E) -> asaga_status {
+        for (auto *c : b->ctx) {
+            const double k = c->n > 0 ? (double)c->nnz / (double)c->n : 0.0;
+            int G = 1;
+            while (G < 4 && k >= 2.0 * G * E) G *= 2;
+            c->row_group = G;
+            c->row_threshold = G > 1 ? 0 : -1;
+        }
+        return batch_layout(b, err);
+    };
+    double best_ms = INFINITY, best_E = 0;
+    TRY(apply(INFINITY));
+    TRY(batch_time_epoch(b, &best_ms, seconds, err));
+    const double t_single = best_ms;
+    best_ms = 0.97 * t_single;
+    for (double E : {512.0, 256.0}) {
+        bool any = false;
+        for (auto *c : b->ctx) any = any || (c->n > 0 && (double)c->nnz / (double)c->n >= 2.0 * E);
+        if (!any) continue;
+        double ms = INFINITY;
+        TRY(apply(E));
+        TRY(batch_time_epoch(b, &ms, seconds, err));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_E = E;
+        }
+    }
+    return apply(best_E > 0 ? best_E : INFINITY);
+}
+
 asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune_result *res, std::string *err) {
     CK(cudaSetDevice(b->device), "cudaSetDevice");
     const int E = trial_epochs > 0 ? std::max(5, (int)std::ceil(trial_epochs)) : 16;
     const int N = b->count;
     int trials = 0;
     double seconds = 0;
+    for (auto *c : b->ctx) {  // the trials run on single-warp cores; the row paths come last
+        c->row_group = 1;
+        c->row_threshold = -1;
+    }
     // 1. steps under the default schedule (equal epoch times)
     TRY(batch_default_schedule(b, err));
     std::vector<int> kc1, kc2;
@@ -2168,10 +2231,18 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
     }
     const std::vector<int> &kc = second ? kc2 : kc1;
     const std::vector<double> &pc = second ? pc2 : pc1;
+    for (int i = 0; i < N; ++i)
+        if (kc[i] != -1000) b->ctx[i]->gamma = b->ctx[i]->gamma_base * std::pow(2.0, -0.5 * kc[i]);
+    // 3. per-instance row paths at the tuned warps and steps (the warps are
+    //    regrouped, not added): every row of instance i on cores of
+    //    G_i = min(4, 2^floor(log2(k_i / E))) warps, k_i its mean row length,
+    //    for E = 512 and 256 entries per warp, against single warps; each
+    //    schedule's batch epoch timed (the faster of two after one untimed),
+    //    the fastest kept if 3% faster
+    TRY(batch_tune_row_paths(b, &seconds, err));
     b->segments_done = 0;  // the tuned state starts at x = 0: the abar cadence restarts
     for (int i = 0; i < N; ++i) {
         asaga_ctx *c = b->ctx[i];
-        if (kc[i] != -1000) c->gamma = c->gamma_base * std::pow(2.0, -0.5 * kc[i]);
         c->warps = b->warps[i];
         TRY(reset_state(c, err));
         if (res) {
@@ -2180,6 +2251,8 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
             res[i].score = std::isfinite(pc[i]) ? 1.0 / pc[i] : -1.0;
             res[i].trials = trials;
             res[i].seconds = seconds;
+            res[i].row_threshold = c->row_threshold;
+            res[i].row_group = c->row_group;
         }
     }
     return ASAGA_OK;
@@ -2336,7 +2409,7 @@ asaga_status asaga_get_state(asaga_ctx *c, float *x, float *abar, float *alpha) 
     if (!c) return ASAGA_EINVAL;
     std::string *err = &c->err;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const size_t pitch = (size_t)c->stride * sizeof(float4);
+    const size_t pitch = (size_t)c->stride * sizeof(float2);
     if (x) CK(cudaMemcpy2DAsync(x, sizeof(float), (const char *)c->state, pitch, sizeof(float), c->d,
                                 cudaMemcpyDeviceToHost, c->stream), "copy x");
     if (abar) CK(cudaMemcpy2DAsync(abar, sizeof(float), (const char *)c->state + sizeof(float), pitch, sizeof(float),
@@ -2352,7 +2425,7 @@ asaga_status asaga_set_state(asaga_ctx *c, const float *x, const float *abar, co
     if (updates_done < 0) return fail(&c->err, ASAGA_EINVAL, "updates_done < 0");
     std::string *err = &c->err;
     CK(cudaSetDevice(c->device), "cudaSetDevice");
-    const size_t pitch = (size_t)c->stride * sizeof(float4);
+    const size_t pitch = (size_t)c->stride * sizeof(float2);
     if (x) CK(cudaMemcpy2DAsync((char *)c->state, pitch, x, sizeof(float), sizeof(float), c->d,
                                 cudaMemcpyHostToDevice, c->stream), "copy x");
     if (abar) CK(cudaMemcpy2DAsync((char *)c->state + sizeof(float), pitch, abar, sizeof(float), sizeof(float), c->d,

@@ -17,11 +17,11 @@ enum ValType : int { kF32 = 1, kBF16 = 2, kF16 = 3, kRowScale = 4 };
 // kIdx16 when the column indices are stored as uint16 (d <= 65536).
 constexpr int kIdx16 = 8;
 
-// Per-column solver state, 16 bytes: the iterate x_v, the running average
-// abar_v and the reweighting D_v, gathered by one 16-byte load and updated
-// (x_v, abar_v) by one vector atomic.  Columns are spaced `stride` float4s
-// apart.
-//   .x = x_v, .y = abar_v, .z = D_v, .w = unused (0)
+// Per-column solver state: the mutable pair float2 {x_v, abar_v} (8 bytes,
+// gathered by one load and updated by one 2-wide vector reduction), columns
+// spaced `stride` float2s apart; and the constant reweighting D_v in an
+// array of its own, read through the non-coherent (L1-cached) path, so that
+// the lines the updates contend for hold only mutable state.
 
 
 // Launch parameters of the asynchronous update kernel (one update = one
@@ -45,8 +45,9 @@ struct UpdateParams {
     const void *values;       // nnz (or n*d) of the storage type, or n row values (kRowScale)
     const float *labels;      // n, float32 copy for the update
     float *alpha;             // n, scalar memory per sample
-    float4 *state;            // d * stride
-    int stride;               // float4s between consecutive columns
+    float2 *state;            // d * stride: {x_v, abar_v}
+    const float *dcol;        // d: D_v
+    int stride;               // float2s between consecutive columns
     int loss;                 // 0 logistic, 1 squared
     float gamma, lambda, inv_n;
     uint64_t seed;            // sampler seed
@@ -80,7 +81,8 @@ struct EvalParams {
     const void *values;       // per entry, or per row (kRowScale)
     const double *labels;     // n, float64
     const float *alpha;       // n
-    float4 *state;
+    float2 *state;            // {x_v, abar_v}, stride float2s apart
+    const float *dcol;        // D_v
     int stride;
     int loss;
     double lambda;
@@ -155,11 +157,11 @@ cudaError_t launch_batch_recompute(const EvalParams *params, int count, int grid
 // prep (eval.cu).  These run while the host is still checking the problem,
 // so they skip columns outside [0, d) and row ranges outside [0, nnz].
 cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int64_t d, int *count, cudaStream_t s);
-// state[v] <- {0, 0, D_v, 0}, D_v = n/count_v (0 if count_v = 0); count may be nullptr (dense: D = 1).
-cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n,
+// state[v] <- {0, 0}, dcol[v] <- D_v = n/count_v (0 if count_v = 0); count may be nullptr (dense: D = 1).
+cudaError_t launch_init_state(float2 *state, float *dcol, int stride, int64_t d, const int *count, int64_t n,
                               cudaStream_t s);
 // out[0] <- max_i (c |a_i|^2 + lambda max_{v in S_i} D_v) (float64) over the stored
-// values; needs D in state.z.  Set-up layout: int32 columns, one value per entry.
+// values; needs D in dcol.  Set-up layout: int32 columns, one value per entry.
 cudaError_t launch_max_row_smoothness(const EvalParams &p, int64_t nnz, int vtype, bool dense, double c_loss, int grid,
                                       double *partial, double *out, cudaStream_t s);
 // dst (vtype) <- src (src_dtype: 0 f64, 1 f32, 2 bf16, 3 f16), count elements.

@@ -75,15 +75,16 @@ template <typename R, typename F> R with_layout(int layout, bool dense, F &&f, R
 
 // Read of shared state at L2 (bypasses L1, which is not coherent with the
 // atomics other SMs apply).
-__device__ __forceinline__ float4 ld_state(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_state(const float2 *p) { return __ldcg(p); }
 
-// Read of state that no thread writes during the kernel (evaluations):
-// L1-cached, non-coherent path.
-__device__ __forceinline__ float4 ld_state_ro(const float4 *p) { return __ldg(p); }
+// Read of state that no thread writes during the kernel (evaluations), and
+// of the constant D: L1-cached, non-coherent path.
+__device__ __forceinline__ float2 ld_state_ro(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float ld_d(const float *p) { return __ldg(p); }
 
 // x_v += dx and abar_v += dab as one vector reduction at L2 (each element
 // is added atomically; nothing is returned).
-__device__ __forceinline__ void red_add_v2(float4 *p, float dx, float dab) {
+__device__ __forceinline__ void red_add_v2(float2 *p, float dx, float dab) {
     asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(dx), "f"(dab)
                  : "memory");
 }

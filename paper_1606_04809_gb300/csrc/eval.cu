@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kEvalBlock) batch_abar_finish_kernel(const Eva
     const EvalParams &e = params[blockIdx.y];
     double local = 0.0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < e.d; v += (int64_t)gridDim.x * blockDim.x) {
-        float4 *sv = e.state + v * e.stride;
+        float2 *sv = e.state + v * e.stride;
         const double exact = e.acc[v];
         local = fmax(local, fabs((double)sv->y - exact));
         sv->y = (float)exact;
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kEvalBlock) column_finish_kernel(const EvalPar
                                                                    double *partial) {
     double local = 0.0;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < P.d; v += (int64_t)gridDim.x * blockDim.x) {
-        float4 *sp = P.state + v * P.stride;
+        float2 *sp = P.state + v * P.stride;
         if (mode == 0) {
             const double g = acc[v] + P.lambda * (double)sp->x;
             acc[v] = g;
@@ -393,11 +393,12 @@ __global__ void __launch_bounds__(256) count_columns_kernel(const int32_t *col, 
         if (key[j] >= 0 && cnt[j] > 0) atomicAdd(count + key[j], cnt[j]);
 }
 
-__global__ void init_state_kernel(float4 *state, int stride, int64_t d, const int *count, int64_t n) {
+__global__ void init_state_kernel(float2 *state, float *dcol, int stride, int64_t d, const int *count, int64_t n) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < d; v += (int64_t)gridDim.x * blockDim.x) {
         float D = 1.f;
         if (count) D = count[v] > 0 ? (float)((double)n / (double)count[v]) : 0.f;
-        state[v * stride] = make_float4(0.f, 0.f, D, 0.f);
+        state[v * stride] = make_float2(0.f, 0.f);
+        dcol[v] = D;
     }
 }
 
@@ -432,7 +433,7 @@ __global__ void __launch_bounds__(kEvalBlock) row_smoothness_kernel(const EvalPa
             s += a * a;
             const int c = kDense ? k : static_cast<const int32_t *>(P.col_idx)[start + k];
             if (c < 0 || c >= P.d) continue;
-            dmax = fmax(dmax, (double)ld_state_ro(P.state + (int64_t)c * P.stride).z);
+            dmax = fmax(dmax, (double)ld_d(P.dcol + c));
         }
         best = fmax(best, c_loss * warp_sum(s) + P.lambda * warp_max(dmax));
     }
@@ -601,8 +602,9 @@ cudaError_t launch_count_columns(const int32_t *col_idx, int64_t nnz, int64_t d,
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_state(float4 *state, int stride, int64_t d, const int *count, int64_t n, cudaStream_t s) {
-    init_state_kernel<<<elementwise_grid(d), 256, 0, s>>>(state, stride, d, count, n);
+cudaError_t launch_init_state(float2 *state, float *dcol, int stride, int64_t d, const int *count, int64_t n,
+                              cudaStream_t s) {
+    init_state_kernel<<<elementwise_grid(d), 256, 0, s>>>(state, dcol, stride, d, count, n);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,10 @@
 // asaga_probe_line_rate: the L2 service time of one column's state line under
 // the update kernel's own access pattern.
 //
-// Every update whose row holds column v reads v's 16-byte state {x, abar,
-// D, 0} (the inconsistent read of x^_v in Algorithm 2) and then adds to x_v
-// and abar_v with one 2-wide float reduction whose value depends on that
-// read.  All such accesses meet at the one L2 slice that owns the line, which
+// Every update whose row holds column v reads v's 8-byte state {x, abar}
+// (the inconsistent read of x^_v in Algorithm 2) and then adds to x_v and
+// abar_v with one 2-wide float reduction whose value depends on that read
+// (D_v, constant, comes from another array through L1).  All such accesses meet at the one L2 slice that owns the line, which
 // serialises them.  A column held by c rows therefore costs an epoch at
 // least c times the service time of one (read, reduction) pair, whatever the
 // number of warps; on a problem whose most frequent column is in almost every
@@ -26,11 +26,11 @@
 namespace asaga {
 namespace {
 
-__global__ void line_probe_kernel(float4 *line, int64_t pairs, int warps) {
+__global__ void line_probe_kernel(float2 *line, int64_t pairs, int warps) {
     const int warp = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (warp >= warps || (threadIdx.x & 31) != 0) return;
     for (int64_t k = 0; k < pairs; ++k) {
-        const float4 s = ld_state(line);
+        const float2 s = ld_state(line);
         // a value that depends on the read and leaves the line's numbers
         // unchanged in practice (the adds are ~1e-30 of the values read)
         red_add_v2(line, s.x * 1e-30f, s.y * 1e-30f);
@@ -47,7 +47,7 @@ extern "C" asaga_status asaga_probe_line_rate(int warps, int64_t pairs, double *
         set_thread_error("warps must be in [1, 65536], pairs >= 1 and ns_per_pair not NULL");
         return ASAGA_EINVAL;
     }
-    float4 *line = nullptr;
+    float2 *line = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaStream_t s = nullptr;
     std::string where;

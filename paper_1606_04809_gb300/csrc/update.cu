@@ -16,7 +16,7 @@
 // abar = (1/n) sum_i alpha_i a_i holds in exact arithmetic under any
 // interleaving of cores.
 //
-// One read per entry.  Every entry's state {x^_v, abar_v, D_v} is gathered
+// One read per entry.  Every entry's state {x^_v, abar_v} and D_v is read
 // once, before any write of the update; the dot product uses x^_v and the
 // scatter uses the term c_v = D_v (abar_v + lambda x^_v) computed from that
 // same read, kept in a register (or, past the register slots of a very long
@@ -43,8 +43,9 @@
 //
 // Layout: A in CSR (int64 row_ptr, int32 or uint16 col_idx, values in
 // fp32/bf16/fp16 or one value per row) or dense row-major; per-column state
-// float4 {x, abar, D, 0}, so one 16-byte L2 read serves x^_v, abar_v and
-// D_v and one 8-byte vector reduction updates x_v and abar_v.
+// float2 {x, abar}, so one 8-byte L2 read serves x^_v and abar_v and one
+// 8-byte vector reduction updates both; D_v, which never changes, comes from
+// an array of its own through the L1-cached read-only path.
 #include <algorithm>
 
 #include "asaga_internal.h"
@@ -425,29 +426,35 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                 }
             }
             if (P.trace && lead) t_read = globaltimer_ns();
-            float4 s[kN];
+            float2 s[kN];
+            float dv[kN];
 #pragma unroll
             for (int q = 0; q < kN; ++q) {
-                s[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (32 * (q * G + w) + lane < len) s[q] = ld_state(P.state + r.c[q] * (int64_t)P.stride);
+                s[q] = make_float2(0.f, 0.f);
+                dv[q] = 0.f;
+                if (32 * (q * G + w) + lane < len) {
+                    s[q] = ld_state(P.state + r.c[q] * (int64_t)P.stride);
+                    dv[q] = ld_d(P.dcol + r.c[q]);
+                }
             }
             if (lead) alpha_hat = __ldcg(P.alpha + h.row);
             const float lambda = P.lambda;
 #pragma unroll
             for (int q = 0; q < kN; ++q) {
                 z = fmaf(r.a[q], s[q].x, z);
-                r.cv[q] = s[q].z * fmaf(lambda, s[q].x, s[q].y);
+                r.cv[q] = dv[q] * fmaf(lambda, s[q].x, s[q].y);
             }
             // entries past the register slots: read once, c_v kept in the scratch
             for (int e = regcap + 32 * w + lane; e < len; e += 32 * G) {
                 int cc;
                 float av;
                 entry_global<T, I, kDense>(P, h.start, h.scale, e, cc, av);
-                const float4 sv = ld_state(P.state + cc * (int64_t)P.stride);
+                const float2 sv = ld_state(P.state + cc * (int64_t)P.stride);
+                const float dcv = ld_d(P.dcol + cc);
                 z = fmaf(av, sv.x, z);
                 const int64_t j = e - regcap;
                 if (tail && j < P.tail_stride)
-                    tail[j] = sv.z * fmaf(lambda, sv.x, sv.y);
+                    tail[j] = dcv * fmaf(lambda, sv.x, sv.y);
                 else
                     scratch_short = true;
             }
@@ -509,10 +516,9 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                 for (int q = 0; q < kN; ++q) {
                     if (32 * (q * G + w) + lane < len) {
                         const float dx = -gamma * fmaf(delta, r.a[q], r.cv[q]);
-                        float4 *ptr = P.state + r.c[q] * (int64_t)P.stride;
-                        const float4 cur_s = ld_state(ptr);
-                        __stcg(reinterpret_cast<float2 *>(ptr),
-                               make_float2(cur_s.x + dx, cur_s.y + delta * r.a[q] * inv_n));
+                        float2 *ptr = P.state + r.c[q] * (int64_t)P.stride;
+                        const float2 cur_s = ld_state(ptr);
+                        __stcg(ptr, make_float2(cur_s.x + dx, cur_s.y + delta * r.a[q] * inv_n));
                     }
                 }
                 for (int e = regcap + 32 * w + lane; e < len; e += 32 * G) {
@@ -520,9 +526,9 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                     float av;
                     entry_global<T, I, kDense>(P, h.start, h.scale, e, cc, av);
                     const float dx = -gamma * fmaf(delta, av, tail[e - regcap]);
-                    float4 *ptr = P.state + cc * (int64_t)P.stride;
-                    const float4 cur_s = ld_state(ptr);
-                    __stcg(reinterpret_cast<float2 *>(ptr), make_float2(cur_s.x + dx, cur_s.y + delta * av * inv_n));
+                    float2 *ptr = P.state + cc * (int64_t)P.stride;
+                    const float2 cur_s = ld_state(ptr);
+                    __stcg(ptr, make_float2(cur_s.x + dx, cur_s.y + delta * av * inv_n));
                 }
                 if (lead && lane == 0) __stcg(P.alpha + h.row, __ldcg(P.alpha + h.row) + delta);
             } else {

@@ -1,6 +1,6 @@
 """The line-rate probe (asaga_probe_line_rate) and the floor it sets.
 
-Every update whose row holds column v reads v's 16-byte state and then adds
+Every update whose row holds column v reads v's 8-byte state and then adds
 to it (Algorithm 2's read of x^_v and write of x_v, abar_v); the L2 slice
 that owns the line serialises those pairs.  The probe measures the time
 per pair once the line is saturated, so an epoch of a problem whose most
