@@ -65,6 +65,7 @@ WORKLOADS = {
 }
 ABAR_EVERY = 5
 TARGET = 1e-6
+L2_BYTES = 129 * 1024 * 1024  # GB300's L2
 # the batch workload (C4): 256 independent l2-logistic instances (a regularisation path)
 BATCH_DESC = ("C4, 256 l2-logistic instances: n~U[10000,200000], d~U[1000,50000], density~U[0.5%,2%] "
               "(rows of about density*d entries), Zipf(1.1) columns, |N(0,1)| row-normalised, lambda on a log "
@@ -96,6 +97,7 @@ def parse():
     ap.add_argument("--compact", type=int, default=0, choices=[0, 1],
                     help="compact storage of A (uint16 indices / one value per row where exact)")
     ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
+    ap.add_argument("--wpb", type=int, default=0, help="with --warps: warps per block (0: eight)")
     return ap.parse_args()
 
 
@@ -298,6 +300,18 @@ def time_cpu_asaga(p, seconds, fstar, target):
             "sample": f"{epochs} epochs from x=0 ({upd:.1f} s of updates)"}
 
 
+def static_config(wl, p, storage, compact, world):
+    """The configuration keys that do not depend on the run (the same on both arms)."""
+    a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
+    side = a_bytes + p.n * (8 + 4 + 8)  # A, row_ptr, labels and the memory
+    return {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
+            "L": wl["L"], "gamma_default": "1/(3L)", "abar_recompute_every": ABAR_EVERY, "compact": compact,
+            "l2": (f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)" if a_bytes > L2_BYTES else
+                   f"inputs ({side / 1e6:.0f} MB) fit in L2: each step timed alone, L2 flushed (a 258 MB write) "
+                   f"between steps outside the timed events"),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args, p, wl):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -310,7 +324,7 @@ def run_reference(args, p, wl):
         "impl": "reference", "metric": "epochs/s", "value": eps, "unit": "epochs/s", "n_gpus": args.gpus,
         "steps": done, "warmup": args.warmup, "ms_per_step": 1e3 * el / done, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["desc"]},
+        "config": static_config(wl, p, p.storage if p.storage != "f64" else "f32", 0, world),
         "cpu_baseline": {"value": eps, "unit": "epochs/s", "cores": 1, "kind": "oracle",
                          "sample": f"{done} steps of n/{per_epoch} serial float64 Sparse SAGA updates, the "
                                    f"float64 objective after every {per_epoch}th, from x=0 ({done / per_epoch:.2f} epochs)"},
@@ -606,7 +620,9 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
         ctx.close()
         opts.update(max_warps=args.warps, gamma=args.gamma_scale / (3.0 * L))
         ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
-        tune = {"fixed": True, "warps": args.warps, "gamma_scale": args.gamma_scale}
+        if args.wpb:
+            asaga.asaga_set_schedule(ctx.ctx, args.warps, args.gamma_scale / (3.0 * L), args.wpb)
+        tune = {"fixed": True, "warps": args.warps, "gamma_scale": args.gamma_scale, "warps_per_block": args.wpb}
     else:
         t_tune = time.perf_counter()
         tune = asaga.asaga_autotune(ctx.ctx)
@@ -625,19 +641,37 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
         pass
     clocks = ClockSampler(uuid)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     solver_s, launches, f_last = 0.0, 0, None
-    e0.record(stream)
-    for _ in range(steps):
-        s, r = asaga.asaga_run(ctx.ctx, 1)
-        solver_s += r.solver_seconds
-        launches += r.kernel_launches
-        f_last = r.f_last
-    e1.record(stream)
-    torch.cuda.synchronize()
+    a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
+    if a_bytes > L2_BYTES:  # inputs larger than L2: one timed region over all steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            s, r = asaga.asaga_run(ctx.ctx, 1)
+            solver_s += r.solver_seconds
+            launches += r.kernel_launches
+            f_last = r.f_last
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_local = e0.elapsed_time(e1)
+    else:  # inputs that fit in L2: every step timed alone, L2 flushed between steps (outside the events)
+        flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+        ms_local = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, r = asaga.asaga_run(ctx.ctx, 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_local += e0.elapsed_time(e1)
+            solver_s += r.solver_seconds
+            launches += r.kernel_launches
+            f_last = r.f_last
+        del flush
     barrier()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
+    ms = max_over_ranks(ms_local)
 
     value = world * steps / (ms * 1e-3)
     upd_ms = 1e3 * solver_s / steps
@@ -711,21 +745,16 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
                "sample": f"{done} epochs of serial float64 Sparse SAGA + objective from x=0 ({el:.1f} s)"}
         cpu["asaga_all_cores"] = time_cpu_asaga(p, cpu_seconds * 2, golden["fstar"] if golden else None, TARGET)
 
-    a_bytes = p.nnz * ({"f32": 4, "bf16": 2, "f16": 2}[storage] + (0 if p.dense else 4))
     return {
         "metric": "epochs/s", "value": value, "unit": "epochs/s", "steps": steps, "warmup": warmup,
         "ms_per_step": ms / steps,
         "dtype": {"f32": "f32 values, f32 state", "bf16": "bf16 values, f32 state",
                   "f16": "f16 values, f32 state"}[storage],
-        "config": {"workload": wl["desc"], "n": p.n, "d": p.d, "nnz": p.nnz, "storage": storage,
-                   "L": wl["L"], "gamma_default": "1/(3L)",
-                   "warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
-                   "gamma_over_gamma0": info["gamma"] * 3.0 * info["L"], "L_value": info["L"],
-                   "row_path": {"threshold": info["row_threshold"], "group": info["row_group"]},
-                   "abar_recompute_every": ABAR_EVERY, "compact": args.compact,
-                   "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"],
-                   "l2": f"inputs larger than L2 (A = {a_bytes / 1e6:.0f} MB > 129 MB)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": static_config(wl, p, storage, args.compact, world),
+        "schedule": {"warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
+                     "gamma_over_gamma0": info["gamma"] * 3.0 * info["L"], "L_value": info["L"],
+                     "row_path": {"threshold": info["row_threshold"], "group": info["row_group"]},
+                     "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"]},
         "time_to_target": ttt,
         "autotune": tune,
         "e2e": e2e,

@@ -1975,14 +1975,17 @@ asaga_status batch_tune_pass(asaga_batch *b, int E, std::vector<int> *kc_out, st
     const int nk = kBottom - kTop + 1;
     const int N = b->count;
     std::vector<double> g0(N), g(N);
+    std::vector<char> live(N, 1);  // instances still running in the current trial
     auto grads = [&](std::vector<double> &out) -> asaga_status {
         for (int i = 0; i < N; ++i) {
+            if (!live[i]) continue;
             TRY(enqueue_grad(b->ctx[i], err));
             CK(cudaMemcpyAsync(b->ctx[i]->hout + 2, b->ctx[i]->dout + 2, sizeof(double), cudaMemcpyDeviceToHost,
                                b->stream), "copy");
         }
         TRY(stream_sync(b->ctx[0], err));
-        for (int i = 0; i < N; ++i) out[i] = b->ctx[i]->hout[2];
+        for (int i = 0; i < N; ++i)
+            if (live[i]) out[i] = b->ctx[i]->hout[2];
         return ASAGA_OK;
     };
     for (auto *c : b->ctx) TRY(reset_state(c, err));
@@ -1993,26 +1996,30 @@ asaga_status batch_tune_pass(asaga_batch *b, int E, std::vector<int> *kc_out, st
         const double scale = std::pow(2.0, -0.5 * k);
         for (auto *c : b->ctx) TRY(reset_state(c, err));
         std::vector<TuneTrial> t(N);
+        std::fill(live.begin(), live.end(), 1);
         for (int e = 1; e <= E; ++e) {
             for (int i = 0; i < N; ++i) {
                 asaga_ctx *c = b->ctx[i];
                 b->h_up[i].gamma = (float)(c->gamma_base * scale);
                 b->h_up[i].t_begin = (uint64_t)c->updates_done;
-                b->h_up[i].count = c->n;
+                b->h_up[i].count = live[i] ? c->n : 0;
             }
             float ms = 0;
             TRY(batch_segment(b, false, &ms, err));
             *seconds += ms * 1e-3;
-            for (auto *c : b->ctx) c->updates_done += c->n;
+            for (int i = 0; i < N; ++i)
+                if (live[i]) b->ctx[i]->updates_done += b->ctx[i]->n;
             TRY(grads(g));
             for (int i = 0; i < N; ++i) {
-                if (t[i].diverged) continue;
+                if (t[i].diverged || !live[i]) continue;
                 t[i].epochs = e;
                 if (!(g0[i] > 0) || !std::isfinite(g[i]) || g[i] > 1e6 * g0[i]) {
                     t[i].diverged = g0[i] > 0;
+                    live[i] = 0;  // diverged: nothing more to learn from this trial
                     continue;
                 }
                 t[i].y.push_back(std::log10(std::max(g[i] / g0[i], 1e-300)));
+                if (t[i].y.back() <= kTuneDeep) live[i] = 0;  // reached the prediction's level: its count is exact
             }
         }
         ++*trials;

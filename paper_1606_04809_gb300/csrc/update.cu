@@ -434,7 +434,7 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                 dv[q] = 0.f;
                 if (32 * (q * G + w) + lane < len) {
                     s[q] = ld_state(P.state + r.c[q] * (int64_t)P.stride);
-                    dv[q] = ld_d(P.dcol + r.c[q]);
+                    dv[q] = kDense ? 1.f : ld_d(P.dcol + r.c[q]);  // a dense column is in every row: D_v = 1
                 }
             }
             if (lead) alpha_hat = __ldcg(P.alpha + h.row);
@@ -450,7 +450,7 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                 float av;
                 entry_global<T, I, kDense>(P, h.start, h.scale, e, cc, av);
                 const float2 sv = ld_state(P.state + cc * (int64_t)P.stride);
-                const float dcv = ld_d(P.dcol + cc);
+                const float dcv = kDense ? 1.f : ld_d(P.dcol + cc);
                 z = fmaf(av, sv.x, z);
                 const int64_t j = e - regcap;
                 if (tail && j < P.tail_stride)
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams
 // inst = the last i with block_begin[i] <= b, whose parameters are copied to
 // shared memory once; its cores split that instance's updates.
 template <typename T, typename I, bool kDense>
-__global__ void __launch_bounds__(kBatchBlock, 6) batch_update_kernel(const UpdateParams *__restrict__ params,
+__global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateParams *__restrict__ params,
                                                                    const int *__restrict__ block_begin, int count) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ UpdateParams sp;
