@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="urllike", choices=sorted(WORKLOADS) + ["batch"])
-    ap.add_argument("--also", default="rcv1like,covtypelike",
+    ap.add_argument("--also", default="rcv1like,covtypelike,batch",
                     help="other configurations measured in the same line (comma separated, 'none' for none)")
     ap.add_argument("--also-steps", type=int, default=100, help="timed steps of each --also configuration")
     ap.add_argument("--single-sample", type=int, default=32,
@@ -200,7 +200,8 @@ def ncu_summary(profile):
         out["traffic"] = int(kv["traffic_bytes_per_launch"])
     except Exception:
         return None
-    for key, name in (("l2_throughput_pct_of_peak", "l2_pct"), ("dram_throughput_pct_of_peak", "dram_pct")):
+    for key, name in (("l2_throughput_pct_of_peak", "l2_pct"), ("dram_throughput_pct_of_peak", "dram_pct"),
+                      ("traffic_bytes_per_full_launch", "traffic_full")):
         if key in kv:
             out[name] = float(kv[key])
     return out
@@ -336,6 +337,93 @@ def run_reference(args, p, wl):
 # ---------------------------------------------------------------- our arm
 
 
+def load_full_batch(specs, indices, gold):
+    """Generates instances `indices` of the full-size batch on the host (C
+    generator, all cores), checks that each is the problem its f* was
+    certified for, moves it to the device and drops the host copy.  Returns
+    (metas: shapes and lambda only, structs over the device arrays, the
+    device arrays, f*)."""
+    import torch
+    from paper_1606_04809_gb300 import asaga
+
+    metas, structs, keep, fs = [], [], [], []
+    for i in indices:
+        p = synth.batch_instance(specs[i], values="bits")
+        g = gold.get(specs[i]["k"])
+        if g is None or g["fingerprint"] != p.fingerprint():
+            raise SystemExit(f"instance {i}: no certified f* for this generated problem")
+        fs.append(g["fstar"])
+        dev = [torch.from_numpy(p.row_ptr).to("cuda"), torch.from_numpy(p.col_idx).to("cuda"),
+               torch.from_numpy(p.values.view(np.int16)).to("cuda"), torch.from_numpy(p.labels).to("cuda")]
+        keep.append(dev)
+        structs.append(asaga.Problem(p.n, p.d, *dev[:3], "bf16", dev[3], on_device=True, nnz=p.nnz))
+        m = synth.Problem(p.name, p.n, p.d, np.array([0, p.nnz]), p.col_idx[:0], p.values[:0], p.labels[:0],
+                          p.loss, p.lam, p.storage)
+        metas.append(m)  # nnz only (the arrays live on the device)
+        del p
+    torch.cuda.synchronize()
+    return metas, structs, keep, np.array(fs)
+
+
+def full_batch_gold():
+    path = os.path.join(ROOT, "tests", "golden", "fstar_batch256_full.json")
+    return {g["k"]: g for g in json.load(open(path))["instances"]} if os.path.exists(path) else {}
+
+
+def batch_throughput(args, steps, env):
+    """The full-size batch (C4) as one more configuration of the default line:
+    every instance generated and resident, the default schedule and steps (no
+    tuning), `steps` timed batch epochs (one graph segment each, the batched
+    abar recomputation every 5th).  Time to 1e-6 needs the batch tuner and
+    takes minutes; --workload batch measures it."""
+    import torch
+    from paper_1606_04809_gb300 import asaga
+    from paper_1606_04809_gb300 import sharding
+
+    world, rank, local, stream, barrier, max_over_ranks = env
+    t_all = time.perf_counter()
+    specs = synth.batch_params(**synth.FULL_BATCH)
+    mine = sharding.rank_instances([s["n"] * s["k_mean"] for s in specs], world, rank)
+    metas, structs, keep, fs = load_full_batch(specs, mine, full_batch_gold())
+    gen_s = time.perf_counter() - t_all
+    b = asaga.Batch(metas, storage="bf16", structs=structs, epochs_per_segment=1, abar_recompute_every=ABAR_EVERY,
+                    cuda_stream=stream.cuda_stream)
+    del structs, keep
+    warps = sum(asaga.asaga_batch_get_info(b.b, i)["warps"] for i in range(b.count))
+    asaga.asaga_batch_run(b.b, b.count, 1)  # warm-up (captures the segment graph)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    seg_s, launches = 0.0, 0
+    e0.record(stream)
+    for _ in range(steps):
+        st, res = asaga.asaga_batch_run(b.b, b.count, 1)
+        seg_s += res[0].solver_seconds
+        launches += res[0].kernel_launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    b.close()
+    hbm_bytes = sum(update_hbm_bytes(m, "bf16") for m in metas)
+    peak, peak_kind = measured_peak_hbm()
+    seg_ms = 1e3 * seg_s / steps
+    ncu = ncu_summary("batch_update_kernel_batch256") or {}
+    return {"metric": "epochs/s", "value": world * steps / (ms * 1e-3), "unit": "epochs/s (whole batch)",
+            "steps": steps, "ms_per_step": ms / steps, "dtype": "bf16 values, f32 state",
+            "instance_epochs_per_s": world * steps * len(mine) / (ms * 1e-3),
+            "config": {"workload": BATCH_DESC, "instances_per_rank": len(mine),
+                       "nnz_per_rank": int(sum(m.nnz for m in metas)), "warps_total": warps,
+                       "schedule": "the default (warps in proportion to n_i (1 + k_i/128), steps 1/(3L_i)), untuned",
+                       "l2": "inputs larger than L2 (A = 47 GB)"},
+            "roofline": {"bound": "hbm", "achieved": hbm_bytes / (seg_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": hbm_bytes / (seg_ms * 1e-3) / 1e9 / peak, "traffic": ncu.get("traffic_full"),
+                         "kernel": "batch segment: batch_update_kernel + the batched objective",
+                         "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": seg_ms, "peak_source": peak_kind},
+            "time_to_target": {"status": "not measured here: `bench.py --workload batch` (tuner, then every "
+                                         "instance to 1e-6)"},
+            "gpu_launches": launches, "setup_seconds": gen_s}
+
+
 def run_batch(args):
     """The 256-instance batch (C4) at its specified size: batched bf16 solve
     of every instance in one persistent, graph-captured launch per segment,
@@ -357,30 +445,11 @@ def run_batch(args):
     specs = synth.batch_params(**synth.FULL_BATCH)
     if args.batch_count:
         specs = specs[: args.batch_count]
-    gold_path = os.path.join(ROOT, "tests", "golden", "fstar_batch256_full.json")
-    gold = {g["k"]: g for g in json.load(open(gold_path))["instances"]} if os.path.exists(gold_path) else {}
+    gold = full_batch_gold()
     mine = sharding.rank_instances([s["n"] * s["k_mean"] for s in specs], world, rank)
     stream = torch.cuda.current_stream()
-    # generate each instance on the host (C generator, all cores), check it is
-    # the problem f* was certified for, move it to the device and drop the host copy
     t0 = time.perf_counter()
-    metas, structs, fs, keep = [], [], [], []
-    for i in mine:
-        p = synth.batch_instance(specs[i], values="bits")
-        g = gold.get(specs[i]["k"])
-        if g is None or g["fingerprint"] != p.fingerprint():
-            raise SystemExit(f"instance {i}: no certified f* for this generated problem")
-        fs.append(g["fstar"])
-        dev = [torch.from_numpy(p.row_ptr).to("cuda"), torch.from_numpy(p.col_idx).to("cuda"),
-               torch.from_numpy(p.values.view(np.int16)).to("cuda"), torch.from_numpy(p.labels).to("cuda")]
-        keep.append(dev)
-        structs.append(asaga.Problem(p.n, p.d, *dev[:3], "bf16", dev[3], on_device=True, nnz=p.nnz))
-        metas.append(synth.Problem(p.name, p.n, p.d, p.row_ptr[:0], p.col_idx[:0], p.values[:0], p.labels[:0],
-                                   p.loss, p.lam, p.storage, meta={"nnz": p.nnz}))
-        metas[-1].row_ptr = np.array([0, p.nnz])  # nnz only (the arrays live on the device)
-        del p
-    fs = np.array(fs)
-    torch.cuda.synchronize()
+    metas, structs, keep, fs = load_full_batch(specs, mine, gold)
     phases["generate_and_copy_s"] = time.perf_counter() - t0
     nnz_mine = int(sum(m.nnz for m in metas))
     print(f"batch: {len(mine)} instances, {nnz_mine} nonzeros generated in {phases['generate_and_copy_s']:.1f} s",
@@ -441,7 +510,7 @@ def run_batch(args):
     achieved = hbm_bytes / (seg_ms * 1e-3) / 1e9
     ncu = ncu_summary("batch_update_kernel_batch256") or {}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu.get("traffic"),
+                "traffic": ncu.get("traffic_full") if not args.batch_count else None,
                 "kernel": "batch segment: batch_update_kernel + the batched objective (one CUDA graph per batch epoch)",
                 "algorithmic_bytes_per_launch": hbm_bytes, "kernel_ms": seg_ms, "peak_source": peak_kind,
                 "l2_throughput_pct_of_peak_ncu": ncu.get("l2_pct"), "dram_throughput_pct_of_peak_ncu": ncu.get("dram_pct")}
@@ -806,6 +875,9 @@ def main():
     # the other single-instance configurations, each with its own line of keys
     others = {}
     for name in [w for w in args.also.split(",") if w and w not in (args.workload, "none")]:
+        if name == "batch":
+            others[name] = batch_throughput(args, min(args.steps, 10), env)
+            continue
         others[name] = measure(args, name, min(args.steps, args.also_steps), args.warmup, min(1, args.e2e_steps),
                                args.cpu_seconds / 2, env)
     if rank == 0:
