@@ -398,9 +398,10 @@ asaga_status asaga_set_schedule(asaga_ctx *ctx, int warps, double gamma, int war
  * entries 32 (q group + w) + l,
  * q = 0, 1, ...; the warps add their partial dot products a_i . x^ in shared
  * memory behind a named barrier and scatter their own entries with the same
- * delta.  A core of g warps holds 256 g entries of a row in registers (128 g
- * for dense rows); every entry's state is still read once per update, the
- * entries past that in a per-core scratch array the library allocates.
+ * delta.  A core of g warps stages 256 g entries of a row in shared memory
+ * and holds them in registers; every entry's state is still read once per
+ * update, the entries past that in a per-core scratch array the library
+ * allocates.
  *   threshold  -1: no row takes the multi-warp path (the default); 0: every
  *              row; T > 0: rows longer than T entries, the others on
  *              single-warp cores.

@@ -34,12 +34,11 @@
 // Staging.  A row's CSR data does not depend on the solver state, so each
 // core requests it ahead of time: lane 0 of the core's first warp copies the
 // row_ptr entries and label of the row four updates ahead (cp.async), and
-// the first 128 G column indices and values of the row two updates ahead
+// the first 256 G column indices and values of the row two updates ahead
 // with one bulk copy per array (cp.async.bulk, the Blackwell copy engine),
 // completed on a per-stage mbarrier that every warp of the core waits on
 // (bounded waits).  The window between reading x^ and writing x, which sets
-// the overlap tau, then holds no staging work.  Entries 128 G .. 256 G - 1
-// of a long sparse row are loaded into registers before the window.
+// the overlap tau, then holds no staging work.
 //
 // Layout: A in CSR (int64 row_ptr, int32 or uint16 col_idx, values in
 // fp32/bf16/fp16 or one value per row) or dense row-major; per-column state
@@ -53,8 +52,7 @@
 
 namespace asaga {
 
-constexpr int kSlots = 4;             // register slots of staged entries (per lane)
-constexpr int kTailSlots = 4;         // register slots loaded from global memory before the window
+constexpr int kSlots = 8;             // register slots per lane: the staged entries of a row
 constexpr int kStages = 4;            // staged CSR slices per core (ring)
 constexpr int kMetaRing = 8;          // staged row_ptr / label entries per core (ring)
 constexpr int kStageEntries = 32 * kSlots;  // entries of a row staged per warp of the core
@@ -88,7 +86,7 @@ struct __align__(16) CoreHdr {
     int xflag[2][kMaxGroup];     // per warp: bit 0 staging copy missing, bit 1 stop requested
 };
 constexpr int kCoreHdrBytes = (int)((sizeof(CoreHdr) + 127) / 128 * 128);
-// staged bytes per array per stage: 128 G entries of <= 4 bytes, plus the
+// staged bytes per array per stage: 256 G entries of <= 4 bytes, plus the
 // slack of rounding the copied range out to 16-byte boundaries
 __host__ __device__ constexpr int stage_array_bytes(int g) { return kStageEntries * 4 * g + 32; }
 __host__ __device__ constexpr int core_ring_bytes(int g) { return kCoreHdrBytes + 2 * kStages * stage_array_bytes(g); }
@@ -96,9 +94,7 @@ __host__ __device__ constexpr int core_ring_bytes(int g) { return kCoreHdrBytes 
 // (+128: the rings start at the first 128-byte boundary of the dynamic shared memory)
 size_t update_smem_bytes(int wpb) { return (size_t)wpb * core_ring_bytes(1) + 128; }
 
-// The batch kernel keeps only the staged slots (more resident blocks); its
-// long rows go to multi-warp cores or past the slots.
-int update_register_slots(bool dense, bool batch) { return dense || batch ? kSlots : kSlots + kTailSlots; }
+int update_register_slots(bool, bool) { return kSlots; }
 
 // ---------------------------------------------------------------- PTX helpers
 
@@ -141,14 +137,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
     return done != 0;
 }
 // Waits for the phase of `bar` with the given parity to complete; gives up
-// (returns false) after kStageWaitNs.
-__device__ __noinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
-    if (mbar_try_wait(bar, parity)) return true;
+// (returns false) after kStageWaitNs.  The first test is inline: the copies
+// were started two updates earlier and have almost always landed.
+__device__ __noinline__ bool mbar_wait_slow(uint64_t *bar, unsigned parity) {
     const uint64_t t0 = globaltimer_ns();
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 15) == 0 && globaltimer_ns() - t0 > kStageWaitNs) return false;
     }
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity) {
+    return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
 }
 // Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
 // from this GPU's global memory into this CTA's shared memory, completing
@@ -263,7 +262,7 @@ __device__ __forceinline__ void stage_meta(const UpdateParams &P, CoreHdr &H, in
 
 // Lane 0 of the core's first warp, once meta slot m has landed: fills the
 // header of stage st and starts the bulk copies of the row's first
-// cap = 128 G column indices and values (the copied range rounded out to
+// cap = 256 G column indices and values (the copied range rounded out to
 // 16-byte boundaries; the allocations of A carry the slack).
 template <typename T, typename I, bool kDense>
 __device__ __forceinline__ void arm_stage(const UpdateParams &P, CoreHdr &H, unsigned char *data, int m, int st,
@@ -406,23 +405,18 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
             const unsigned char *colbuf = data + (size_t)st * stage_array_bytes(G);
             const unsigned char *valbuf = data + (size_t)(kStages + st) * stage_array_bytes(G);
             const int len = h.len;
-            // the row's data (not the solver state): staged part from shared
-            // memory, the next 128 G entries from global memory
+            // the row's data (not the solver state), staged in shared memory
 #pragma unroll
             for (int q = 0; q < kN; ++q) {
                 const int e = 32 * (q * G + w) + lane;
                 r.c[q] = 0;
                 r.a[q] = 0.f;
                 if (e < len) {
-                    if (q < kSlots) {
-                        r.c[q] = kDense ? e : raw_col<I>(colbuf, h.col_off + e);
-                        if constexpr (IsRowScale<T>::value)
-                            r.a[q] = h.scale;
-                        else
-                            r.a[q] = raw_value<T>(valbuf, h.val_off + e);
-                    } else {
-                        entry_global<T, I, kDense>(P, h.start, h.scale, e, r.c[q], r.a[q]);
-                    }
+                    r.c[q] = kDense ? e : raw_col<I>(colbuf, h.col_off + e);
+                    if constexpr (IsRowScale<T>::value)
+                        r.a[q] = h.scale;
+                    else
+                        r.a[q] = raw_value<T>(valbuf, h.val_off + e);
                 }
             }
             if (P.trace && lead) t_read = globaltimer_ns();
@@ -604,7 +598,7 @@ __device__ __forceinline__ void run_block(const UpdateParams &P, unsigned char *
 template <typename T, typename I, bool kDense>
 __global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_block<T, I, kDense, kDense ? kSlots : kSlots + kTailSlots>(P, smem, (int)blockIdx.x);
+    run_block<T, I, kDense, kSlots>(P, smem, (int)blockIdx.x);
 }
 
 // Many independent problems in one launch: block b serves instance
@@ -630,12 +624,20 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
     run_block<T, I, kDense, kSlots>(sp, smem, (int)blockIdx.x - s_first);
 }
 
+// Dynamic shared memory beyond 48 KB must be allowed per kernel.
+template <typename K> cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 struct UpdateLaunch {
     const UpdateParams &p;
     int grid;
     cudaStream_t s;
     template <typename T, typename I, bool kDense> cudaError_t run() const {
-        update_kernel<T, I, kDense><<<grid, 32 * p.wpb, update_smem_bytes(p.wpb), s>>>(p);
+        const size_t smem = update_smem_bytes(p.wpb);
+        const cudaError_t e = allow_smem(update_kernel<T, I, kDense>, smem);
+        if (e != cudaSuccess) return e;
+        update_kernel<T, I, kDense><<<grid, 32 * p.wpb, smem, s>>>(p);
         return cudaGetLastError();
     }
 };
@@ -652,8 +654,10 @@ struct BatchUpdateLaunch {
     int count, grid;
     cudaStream_t s;
     template <typename T, typename I, bool kDense> cudaError_t run() const {
-        batch_update_kernel<T, I, kDense>
-            <<<grid, kBatchBlock, update_smem_bytes(kBatchBlock / 32), s>>>(params, block_begin, count);
+        const size_t smem = update_smem_bytes(kBatchBlock / 32);
+        const cudaError_t e = allow_smem(batch_update_kernel<T, I, kDense>, smem);
+        if (e != cudaSuccess) return e;
+        batch_update_kernel<T, I, kDense><<<grid, kBatchBlock, smem, s>>>(params, block_begin, count);
         return cudaGetLastError();
     }
 };
@@ -668,11 +672,20 @@ struct UpdateOccupancy {
     bool batch;
     template <typename T, typename I, bool kDense> int run() const {
         int nb = 0;
-        const cudaError_t e =
-            batch ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_update_kernel<T, I, kDense>, kBatchBlock,
-                                                                  update_smem_bytes(kBatchBlock / 32))
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, I, kDense>, kUpdateBlock,
-                                                                  update_smem_bytes(kUpdateBlock / 32));
+        cudaError_t e;
+        if (batch) {
+            const size_t smem = update_smem_bytes(kBatchBlock / 32);
+            e = allow_smem(batch_update_kernel<T, I, kDense>, smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_update_kernel<T, I, kDense>, kBatchBlock,
+                                                                  smem);
+        } else {
+            const size_t smem = update_smem_bytes(kUpdateBlock / 32);
+            e = allow_smem(update_kernel<T, I, kDense>, smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, I, kDense>, kUpdateBlock,
+                                                                  smem);
+        }
         return e == cudaSuccess && nb > 0 ? nb : 1;
     }
 };
