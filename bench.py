@@ -98,6 +98,8 @@ def parse():
                     help="compact storage of A (uint16 indices / one value per row where exact)")
     ap.add_argument("--gamma-scale", type=float, default=1.0, help="with --warps: step = scale / (3L)")
     ap.add_argument("--wpb", type=int, default=0, help="with --warps: warps per block (0: eight)")
+    ap.add_argument("--draw-ahead", type=int, default=0, choices=[0, 1],
+                    help="with --warps: draw the next row while an update's gathers are in flight")
     return ap.parse_args()
 
 
@@ -691,7 +693,9 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
         ctx = asaga.Context(p, storage=storage, values_dtype=storage if storage != "f16" else "f64", **opts)
         if args.wpb:
             asaga.asaga_set_schedule(ctx.ctx, args.warps, args.gamma_scale / (3.0 * L), args.wpb)
-        tune = {"fixed": True, "warps": args.warps, "gamma_scale": args.gamma_scale, "warps_per_block": args.wpb}
+        asaga.asaga_set_draw_ahead(ctx.ctx, args.draw_ahead)
+        tune = {"fixed": True, "warps": args.warps, "gamma_scale": args.gamma_scale, "warps_per_block": args.wpb,
+                "draw_ahead": args.draw_ahead}
     else:
         t_tune = time.perf_counter()
         tune = asaga.asaga_autotune(ctx.ctx)
@@ -799,6 +803,7 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
             c = asaga.asaga_create(prob, o)
             asaga.asaga_set_schedule(c, info["warps"], info["gamma"], info["warps_per_block"])
             asaga.asaga_set_row_path(c, info["row_threshold"], info["row_group"])
+            asaga.asaga_set_draw_ahead(c, info["draw_ahead"])
             asaga.asaga_run(c, 1)
             asaga.load().asaga_get_state(c, xh.data_ptr(), None, None)
             asaga.asaga_destroy(c)
@@ -823,6 +828,7 @@ def measure(args, name, steps, warmup, e2e_steps, cpu_seconds, env):
         "schedule": {"warps": info["warps"], "warps_per_block": info["warps_per_block"], "gamma": info["gamma"],
                      "gamma_over_gamma0": info["gamma"] * 3.0 * info["L"], "L_value": info["L"],
                      "row_path": {"threshold": info["row_threshold"], "group": info["row_group"]},
+                     "draw_ahead": info["draw_ahead"],
                      "col_index_bytes": info["col_index_bytes"], "row_values": info["row_values"]},
         "time_to_target": ttt,
         "autotune": tune,

@@ -179,6 +179,8 @@ typedef struct {
     int64_t row_threshold; /* rows longer than this take the multi-warp row path
                               (0: every row; -1: none; see asaga_set_row_path)  */
     int row_group;       /* warps per core of the multi-warp row path (1: none)  */
+    int draw_ahead;      /* 1: each core draws its next row while an update's
+                            gathers are in flight (asaga_set_draw_ahead)        */
 } asaga_info;
 
 /* Outcome of asaga_autotune. */
@@ -190,6 +192,7 @@ typedef struct {
     double seconds;      /* device time spent in the trials                      */
     int64_t row_threshold; /* chosen row path (asaga_set_row_path): threshold... */
     int row_group;       /* ...and warps per multi-warp core                     */
+    int draw_ahead;      /* chosen draw placement (asaga_set_draw_ahead)         */
 } asaga_tune_result;
 
 /* Fills *opt with defaults: logistic, lambda 0, gamma 1/(3L), F32 storage,
@@ -270,7 +273,12 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     rows longer than T = 128, 256, 512 entries (when they hold at least 2%
  *     of the nonzeros), each timed over two epochs after one untimed; the
  *     two fastest that beat single warps by 3% run a race trial in turn,
- *     and the first whose predicted time beats the winner's by 3% is kept.
+ *     and the first whose predicted time beats the winner's by 3% is kept;
+ *  6. the draw placement at the winner (asaga_set_draw_ahead): one trial of
+ *     twice the race length with the next row drawn inside the updates'
+ *     windows, kept if it converges and its predicted time beats the
+ *     winner's by 3% (the longer window adds overlap, which can put the
+ *     same warps and step past the frontier).
  * If no trial converges, the defaults stay.  score = 1 / (predicted
  * seconds of the winner), -1 when none settled.  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
@@ -420,6 +428,20 @@ asaga_status asaga_set_schedule(asaga_ctx *ctx, int warps, double gamma, int war
  * 0 applies: threshold 0 replays the updates on one core of `group` warps.
  * EINVAL on other values.  asaga_autotune chooses this too (its step 5). */
 asaga_status asaga_set_row_path(asaga_ctx *ctx, int64_t threshold, int group);
+
+/* Where each core draws the row it stages next (Algorithm 2 samples i
+ * before the update's reads; the draw of a later row can go anywhere).
+ * 0 (default): at the top of an update, before its reads, so the interval
+ * between the reads of x^ and the writes (the window whose overlap with
+ * other updates is the tau of Assumption 1) holds no sampling work.  1: the
+ * first warp of the core draws it while the update's gathers are in flight,
+ * hiding the sampler's latency at the cost of a longer window: faster epochs
+ * at the same warps and step, and more overlap, which can move the same
+ * warps and step past the stability frontier.  The rows drawn and their
+ * order are the same in both placements (a replay in order gives the same
+ * iterate).  asaga_autotune chooses it (its step 6) and resets it to 0
+ * first.  EINVAL: on not 0 or 1. */
+asaga_status asaga_set_draw_ahead(asaga_ctx *ctx, int on);
 
 /* Reason for the last failure of a call on ctx (or, when ctx is NULL, of
  * the calling thread's last asaga_create, asaga_sample_rows,

@@ -68,7 +68,7 @@ class asaga_info(ctypes.Structure):
                 ("column_stride", ctypes.c_int), ("device_bytes", ctypes.c_int64),
                 ("max_row_len", ctypes.c_int64), ("n_hot", ctypes.c_int), ("warps_per_block", ctypes.c_int),
                 ("col_index_bytes", ctypes.c_int), ("row_values", ctypes.c_int),
-                ("row_threshold", ctypes.c_int64), ("row_group", ctypes.c_int)]
+                ("row_threshold", ctypes.c_int64), ("row_group", ctypes.c_int), ("draw_ahead", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -77,7 +77,7 @@ class asaga_info(ctypes.Structure):
 class asaga_tune_result(ctypes.Structure):
     _fields_ = [("warps", ctypes.c_int), ("gamma", ctypes.c_double), ("score", ctypes.c_double),
                 ("trials", ctypes.c_int), ("seconds", ctypes.c_double), ("row_threshold", ctypes.c_int64),
-                ("row_group", ctypes.c_int)]
+                ("row_group", ctypes.c_int), ("draw_ahead", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -143,6 +143,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     L.asaga_set_schedule.restype = i32
     L.asaga_set_row_path.argtypes = [vp, i64, i32]
     L.asaga_set_row_path.restype = i32
+    L.asaga_set_draw_ahead.argtypes = [vp, i32]
+    L.asaga_set_draw_ahead.restype = i32
     L.asaga_batch_set_row_paths.argtypes = [vp, vp, vp]
     L.asaga_batch_set_row_paths.restype = i32
     L.asaga_batch_reset.argtypes = [vp]
@@ -274,6 +276,11 @@ def asaga_set_schedule(ctx: int, warps: int, gamma: float, warps_per_block: int 
 def asaga_set_row_path(ctx: int, threshold: int, group: int) -> None:
     """Rows longer than `threshold` entries (0: all, -1: none) on cores of `group` warps."""
     _check(ctx, load().asaga_set_row_path(ctx, int(threshold), int(group)))
+
+
+def asaga_set_draw_ahead(ctx: int, on: int) -> None:
+    """1: each core draws its next row while an update's gathers are in flight."""
+    _check(ctx, load().asaga_set_draw_ahead(ctx, int(on)))
 
 
 def asaga_cancel(ctx: int) -> None:

@@ -45,6 +45,8 @@ struct asaga_ctx {
     // are updated by cores of row_group warps (the multi-warp row path)
     int row_group = 1;
     int64_t row_threshold = -1;
+    // 1: the next row is drawn while an update's gathers are in flight
+    int draw_ahead = 0;
     uint32_t *long_bits = nullptr;   // bit i: row i is longer than bits_threshold
     int64_t bits_threshold = -1;     // the threshold long_bits was built for (-1: not built)
     double long_share = 0;           // fraction of the nonzeros in rows longer than bits_threshold
@@ -813,6 +815,7 @@ UpdateParams update_params(const asaga_ctx *c) {
     u.idx = nullptr;
     u.fence_each = c->warps == 1 ? 1 : 0;
     u.plain_writes = c->plain_writes ? 1 : 0;
+    u.draw_ahead = c->draw_ahead;
     u.sampling = c->sampling;
     u.deadline_ns = 0;
     u.status = c->status;
@@ -1262,6 +1265,7 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     if (!std::isfinite(trial_epochs)) return fail(err, ASAGA_EINVAL, "trial_epochs must be finite");
     c->row_threshold = -1;  // the trials run on single-warp cores; the row path comes last
     c->row_group = 1;
+    c->draw_ahead = 0;      // and the draw placement after it
     CK(cudaSetDevice(c->device), "cudaSetDevice");
     const int E_race = trial_epochs > 0 ? std::max(4, (int)std::ceil(trial_epochs)) : 24;
     const int E_probe = std::min(16, E_race);
@@ -1460,11 +1464,26 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
             c->row_group = keep_G;
         }
     }
+    // 6. the draw placement at the winner: the next row drawn inside the
+    //    updates' windows hides the sampler's latency but lengthens the
+    //    windows (more overlap at the same warps), so it must converge over
+    //    a trial twice the race length and beat the winner by 3%
+    if (std::isfinite(best_ms)) {
+        c->draw_ahead = 1;
+        TuneTrial t;
+        TRY(run(best_w, best_k, 2 * E_race, kTuneDeep, 1.5 * best_ms, &t));
+        const double ms = predict_epochs(t) * t.ms_per_epoch();
+        if (!t.diverged && converging(t) && std::isfinite(ms) && ms < 0.97 * best_ms)
+            best_ms = ms;
+        else
+            c->draw_ahead = 0;
+    }
     if (std::isfinite(best_ms)) r.score = 1e3 / best_ms;
     r.warps = best_w;
     r.gamma = step(best_k);
     r.row_threshold = c->row_threshold;
     r.row_group = c->row_group;
+    r.draw_ahead = c->draw_ahead;
     TRY(reset_state(c, err));
     c->warps = r.warps;
     c->gamma = r.gamma;
@@ -2260,6 +2279,7 @@ asaga_status batch_autotune_impl(asaga_batch *b, double trial_epochs, asaga_tune
             res[i].seconds = seconds;
             res[i].row_threshold = c->row_threshold;
             res[i].row_group = c->row_group;
+            res[i].draw_ahead = c->draw_ahead;
         }
     }
     return ASAGA_OK;
@@ -2496,6 +2516,14 @@ asaga_status asaga_get_info(asaga_ctx *c, asaga_info *info) {
     info->row_values = (c->layout & ~kIdx16) == kRowScale ? 1 : 0;
     info->row_threshold = c->row_threshold;
     info->row_group = c->row_group;
+    info->draw_ahead = c->draw_ahead;
+    return ASAGA_OK;
+}
+
+asaga_status asaga_set_draw_ahead(asaga_ctx *c, int on) {
+    if (!c) return ASAGA_EINVAL;
+    if (on != 0 && on != 1) return fail(&c->err, ASAGA_EINVAL, "on must be 0 or 1");
+    c->draw_ahead = on;
     return ASAGA_OK;
 }
 

@@ -66,6 +66,7 @@ struct UpdateParams {
     const int64_t *idx;       // explicit row sequence (deterministic replay) or nullptr
     int fence_each;           // 1: fence after every update (single-core order)
     int plain_writes;         // 1: non-atomic load-add-store instead of reductions (diagnostic)
+    int draw_ahead;           // 1: the next row is drawn while the update's gathers are in flight
     uint64_t deadline_ns;     // %globaltimer deadline, 0 = none
     const volatile int *cancel;  // nonzero: stop (a flag in mapped host memory), or nullptr
     int *status;              // bit 0: timed out, bit 1: bad index, bit 2: malformed row range, bit 3: cancelled,

@@ -351,13 +351,22 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
     bool bad = false;
     RowCursor cur;
     int64_t armed = -1;  // last row index (in this core's order) whose stage was armed
+    // With P.draw_ahead the first warp draws the row to stage next while the
+    // update's gathers are in flight (the sampler's latency is hidden, but
+    // the interval between the update's reads and writes grows); otherwise
+    // at the top of the update, before its reads.
+    const bool draw_ahead = P.draw_ahead != 0;
+    int64_t next_i = -1, next_t = -1;  // the row drawn ahead (draw_ahead), -1 once the rows ran out
     // prologue: row_ptr entries of rows 0..3, then the slices of rows 0 and 1
     if (lead) {
+        int64_t last = -1;
         for (int k = 0; k < 4; ++k) {
             int64_t t;
             const int64_t i = next_row(P, cur, core, ncores, is_long, lane, bad, t);
             stage_meta<T, kDense>(P, H, k, i, t, lane);
+            last = i;
         }
+        if (draw_ahead && last >= 0) next_i = next_row(P, cur, core, ncores, is_long, lane, bad, next_t);
         if (lane == 0) {
             cp_async_wait_all();
             arm_stage<T, I, kDense>(P, H, data, 0, 0, cap, G);
@@ -376,15 +385,18 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
             // the slice of row k + 2 (its meta was committed two updates ago)
             // and the meta of row k + 4, before this update's reads: the
             // window between its reads and writes then holds no staging work
+            // (with draw_ahead, row k + 4 was drawn inside the previous one)
             if (lane == 0) {
                 cp_async_wait_all_but_newest();
                 arm_stage<T, I, kDense>(P, H, data, (int)((k + 2) & (kMetaRing - 1)), (int)((k + 2) & (kStages - 1)),
                                         cap, G);
             }
             armed = k + 2;
-            int64_t t;
-            const bool more = H.m_row[(k + 3) & (kMetaRing - 1)] >= 0;
-            const int64_t i = more ? next_row(P, cur, core, ncores, is_long, lane, bad, t) : (t = -1, -1);
+            int64_t i = next_i, t = next_t;
+            if (!draw_ahead) {
+                const bool more = H.m_row[(k + 3) & (kMetaRing - 1)] >= 0;
+                i = more ? next_row(P, cur, core, ncores, is_long, lane, bad, t) : (t = -1, -1);
+            }
             stage_meta<T, kDense>(P, H, (int)((k + 4) & (kMetaRing - 1)), i, t, lane);
             if (lane == 0) cp_async_commit();
             __syncwarp();
@@ -431,7 +443,11 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
                     dv[q] = kDense ? 1.f : ld_d(P.dcol + r.c[q]);  // a dense column is in every row: D_v = 1
                 }
             }
-            if (lead) alpha_hat = __ldcg(P.alpha + h.row);
+            if (lead) {
+                alpha_hat = __ldcg(P.alpha + h.row);
+                if (draw_ahead)  // the row after the one staged above
+                    next_i = next_i >= 0 ? next_row(P, cur, core, ncores, is_long, lane, bad, next_t) : -1;
+            }
             const float lambda = P.lambda;
 #pragma unroll
             for (int q = 0; q < kN; ++q) {
@@ -454,6 +470,8 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
             }
             z = warp_sum(z);
             alpha_hat = __shfl_sync(kFull, alpha_hat, 0);
+        } else if (lead && draw_ahead) {
+            next_i = next_i >= 0 ? next_row(P, cur, core, ncores, is_long, lane, bad, next_t) : -1;
         }
         if (__any_sync(kFull, scratch_short)) {
             if (lane == 0) atomicOr(P.status, 32);

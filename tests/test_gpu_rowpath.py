@@ -74,9 +74,10 @@ def long_rows(n=3000, d=6000, seed=40, **kw):
     return synth.sparse_logistic(n, d, **args)
 
 
-def replay(p, idx, threshold, group, storage="f32"):
+def replay(p, idx, threshold, group, storage="f32", draw_ahead=0):
     with asaga.Context(p, storage=storage) as c:
         asaga.asaga_set_row_path(c.ctx, threshold, group)
+        asaga.asaga_set_draw_ahead(c.ctx, draw_ahead)
         info = asaga.asaga_get_info(c.ctx)
         assert (info["row_threshold"], info["row_group"]) == ((threshold, group) if group > 1 else (-1, 1))
         asaga.asaga_run_indices(c.ctx, idx)
@@ -100,6 +101,16 @@ def test_replay_long_rows_on_one_core_of_group_warps(group):
     assert lens.min() >= 300 and lens.max() > 1024  # past the register slots of G = 1, 2, 4
     idx = synth.sample_indices(p.n, p.n, seed=41)
     got, st = replay(p, idx, 0 if group > 1 else -1, group)
+    assert_close(got, st)
+
+
+@pytest.mark.parametrize("group", [1, 2, 8])
+def test_replay_with_the_row_drawn_ahead(group):
+    """The next row drawn while the gathers are in flight: the same rows in
+    the same order, on single- and multi-warp cores."""
+    p = long_rows(n=2000, seed=49)
+    idx = synth.sample_indices(p.n, p.n, seed=42)
+    got, st = replay(p, idx, 0 if group > 1 else -1, group, draw_ahead=1)
     assert_close(got, st)
 
 
@@ -151,15 +162,20 @@ def long_problem():
     return p, R.objective(p, xs)
 
 
-@pytest.mark.parametrize("path", [(-1, 1), (0, 2), (0, 4), (0, 8), (450, 4)])
+@pytest.mark.parametrize("path", [(-1, 1, 0), (0, 2, 0), (0, 4, 0), (0, 8, 0), (450, 4, 0), (-1, 1, 1), (450, 4, 1)])
 def test_async_long_rows_reach_1e6(long_problem, path):
     """Concurrent cores on rows of 300..1224 entries: every entry's x^ read once
-    per update, its lambda term from that read, on either row path.  The path
-    regroups the tuned warps into cores (same warps, same step)."""
+    per update, its lambda term from that read, on either row path and either
+    draw placement.  The path regroups the tuned warps into cores (same warps,
+    same step)."""
     p, fstar = long_problem
     with asaga.Context(p, seed=6, abar_recompute_every=5) as c:
         tune = asaga.asaga_autotune(c.ctx)
-        asaga.asaga_set_row_path(c.ctx, *path)
+        if path[2] and not tune["draw_ahead"]:  # a longer window: half the step keeps these warps inside the frontier
+            wpb = asaga.asaga_get_info(c.ctx)["warps_per_block"]
+            asaga.asaga_set_schedule(c.ctx, tune["warps"], tune["gamma"] / 2, wpb)
+        asaga.asaga_set_row_path(c.ctx, path[0], path[1])
+        asaga.asaga_set_draw_ahead(c.ctx, path[2])
         s, r = asaga.asaga_run(c.ctx, 400, 1e-6, fstar)
         info = asaga.asaga_get_info(c.ctx)
         x = asaga.asaga_get_state(c.ctx)[0]
@@ -174,6 +190,7 @@ def test_autotune_reports_the_row_path_it_keeps(long_problem):
         tune = asaga.asaga_autotune(c.ctx)
         info = asaga.asaga_get_info(c.ctx)
     assert (tune["row_threshold"], tune["row_group"]) == (info["row_threshold"], info["row_group"])
+    assert tune["draw_ahead"] == info["draw_ahead"] in (0, 1)
     assert tune["row_group"] in (1, 2, 4, 8)
     assert (tune["row_group"] == 1) == (tune["row_threshold"] == -1)
 

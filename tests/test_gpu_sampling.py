@@ -53,9 +53,11 @@ def test_permutation_sampler_visits_every_row_once_per_epoch(n):
         assert c.min() == 1 and c.max() == 1
 
 
-def run_pair(p, sampling, seed, epochs=1):
+def run_pair(p, sampling, seed, epochs=1, draw_ahead=0):
     gamma = 1.0 / (3.0 * R.lipschitz(p))
     with asaga.Context(p, storage="f32", deterministic=1, seed=seed, gamma=gamma, sampling=sampling) as c:
+        asaga.asaga_set_draw_ahead(c.ctx, draw_ahead)
+        assert asaga.asaga_get_info(c.ctx)["draw_ahead"] == draw_ahead
         asaga.asaga_run(c.ctx, epochs)
         x, abar, alpha = asaga.asaga_get_state(c.ctx)
     rows = (R.sampler_indices if sampling == "uniform" else R.permutation_indices)(seed, p.n, 0, epochs * p.n)
@@ -63,11 +65,14 @@ def run_pair(p, sampling, seed, epochs=1):
     return (x, abar, alpha), st
 
 
+@pytest.mark.parametrize("draw_ahead", [0, 1])
 @pytest.mark.parametrize("sampling", ["uniform", "permutation"])
-def test_single_warp_run_with_its_own_sampler_matches_the_checker(sampling):
+def test_single_warp_run_with_its_own_sampler_matches_the_checker(sampling, draw_ahead):
+    """Either draw placement (before an update's reads, or while its gathers
+    are in flight) visits the sampler's rows in its order."""
     p = synth.small_logistic()
     p.values = synth.to_storage_grid(p.values, "f32")
-    (x, abar, alpha), st = run_pair(p, sampling, seed=31)
+    (x, abar, alpha), st = run_pair(p, sampling, seed=31, draw_ahead=draw_ahead)
     assert rel(x, st.x) <= DET_TOL, rel(x, st.x)
     assert rel(alpha, st.alpha) <= DET_TOL
     assert rel(abar, st.abar) <= DET_TOL
@@ -91,4 +96,22 @@ def test_async_permutation_sampling_reaches_1e6():
     with asaga.Context(p, seed=3, sampling="permutation", abar_recompute_every=5) as c:
         asaga.asaga_autotune(c.ctx)
         s, r = asaga.asaga_run(c.ctx, 300, 1e-6, fstar)
+    assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict())
+
+
+def test_draw_ahead_argument_is_checked():
+    p = synth.small_logistic()
+    with asaga.Context(p) as c:
+        with pytest.raises(asaga.AsagaError) as e:
+            asaga.asaga_set_draw_ahead(c.ctx, 2)
+        assert e.value.status == asaga.EINVAL
+        assert asaga.asaga_get_info(c.ctx)["draw_ahead"] == 0
+
+
+def test_async_run_with_the_row_drawn_ahead_reaches_1e6():
+    p = synth.rcv1_like(seed=24, n=50000, d=5000)
+    cert = R.certified_fstar(p, lambda ep: synth.sample_indices(p.n, p.n, 31, ep), rel_tol=1e-10)
+    with asaga.Context(p, seed=5, max_warps=64, abar_recompute_every=5) as c:
+        asaga.asaga_set_draw_ahead(c.ctx, 1)
+        s, r = asaga.asaga_run(c.ctx, 150, 1e-6, cert["fstar"])
     assert s == asaga.OK, (asaga.STATUS_NAMES[s], r.as_dict())
