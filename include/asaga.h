@@ -274,11 +274,12 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     of the nonzeros), each timed over two epochs after one untimed; the
  *     two fastest that beat single warps by 3% run a race trial in turn,
  *     and the first whose predicted time beats the winner's by 3% is kept;
- *  6. the draw placement at the winner (asaga_set_draw_ahead): one trial of
- *     twice the race length with the next row drawn inside the updates'
- *     windows, kept if it converges and its predicted time beats the
- *     winner's by 3% (the longer window adds overlap, which can put the
- *     same warps and step past the frontier).
+ *  6. the draw placement at the winner (asaga_set_draw_ahead): two trials
+ *     of twice the race length with the next row drawn inside the updates'
+ *     windows; kept if both bring |grad f|^2 down by 1e11 and the slower
+ *     one's predicted time beats the winner's by 3% (the longer window adds
+ *     overlap, which can put the same warps and step past the frontier, and
+ *     such a run can fall steadily for dozens of epochs before it stalls).
  * If no trial converges, the defaults stay.  score = 1 / (predicted
  * seconds of the winner), -1 when none settled.  Leaves the state at x = 0,
  * alpha = 0, abar = 0 (sampler position 0) with the chosen pair in use.
