@@ -276,8 +276,9 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     and the first whose predicted time beats the winner's by 3% is kept;
  *  6. the draw placement at the winner (asaga_set_draw_ahead): two trials
  *     of twice the race length with the next row drawn inside the updates'
- *     windows; kept if both bring |grad f|^2 down by 1e11 and the slower
- *     one's predicted time beats the winner's by 3% (the longer window adds
+ *     windows; kept if both bring |grad f|^2 down by 1e10 and the slower
+ *     one's update time to that level beats the winner's prediction by 3%
+ *     (the longer window adds
  *     overlap, which can put the same warps and step past the frontier, and
  *     such a run can fall steadily for dozens of epochs before it stalls).
  * If no trial converges, the defaults stay.  score = 1 / (predicted

@@ -1470,16 +1470,16 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     //    can turn a converging schedule into one that stalls after a long
     //    downward trend (measured: RCV1-shaped rows at the tuned 512 warps),
     //    so a trend is not enough: each of two trials of twice the race
-    //    length must reach one decade below the prediction level, and the
-    //    slower must beat the winner by 3%
+    //    length must reach the prediction level itself, and the slower must
+    //    beat the winner by 3%
     if (std::isfinite(best_ms)) {
         c->draw_ahead = 1;
         double worst = 0;
         for (int trial = 0; trial < 2 && std::isfinite(worst); ++trial) {
             TuneTrial t;
-            TRY(run(best_w, best_k, 2 * E_race, kTuneDeep - 1.0, 2.0 * best_ms, &t));
-            const bool deep = !t.diverged && !t.y.empty() && t.y.back() <= kTuneDeep - 1.0;
-            worst = deep ? std::max(worst, predict_epochs(t) * t.ms_per_epoch()) : INFINITY;
+            TRY(run(best_w, best_k, 2 * E_race, kTuneDeep, best_ms, &t));
+            const bool deep = !t.diverged && !t.y.empty() && t.y.back() <= kTuneDeep;
+            worst = deep ? std::max(worst, t.t_ms) : INFINITY;  // the update time to the level
         }
         if (std::isfinite(worst) && worst < 0.97 * best_ms)
             best_ms = worst;

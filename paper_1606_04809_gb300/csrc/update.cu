@@ -335,8 +335,10 @@ __device__ __forceinline__ void entry_global(const UpdateParams &P, int64_t star
         a = to_f32(ld_stream(static_cast<const T *>(P.values) + start + e));
 }
 
-// One core's share of a launch.
-template <typename T, typename I, bool kDense, int kN>
+// One core's share of a launch.  kAhead: the draw placement (P.draw_ahead),
+// a template parameter so that the default placement compiles as if the
+// option did not exist.
+template <typename T, typename I, bool kDense, int kN, bool kAhead>
 __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, unsigned char *data, int G, int w,
                                              int lane, int core, int ncores, int core_uid, bool is_long, int bar_id) {
     const int cap = kStageEntries * G;  // staged entries of a row
@@ -355,7 +357,7 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
     // update's gathers are in flight (the sampler's latency is hidden, but
     // the interval between the update's reads and writes grows); otherwise
     // at the top of the update, before its reads.
-    const bool draw_ahead = P.draw_ahead != 0;
+    constexpr bool draw_ahead = kAhead;
     int64_t next_i = -1, next_t = -1;  // the row drawn ahead (draw_ahead), -1 once the rows ran out
     // prologue: row_ptr entries of rows 0..3, then the slices of rows 0 and 1
     if (lead) {
@@ -393,7 +395,7 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
             }
             armed = k + 2;
             int64_t i = next_i, t = next_t;
-            if (!draw_ahead) {
+            if constexpr (!draw_ahead) {
                 const bool more = H.m_row[(k + 3) & (kMetaRing - 1)] >= 0;
                 i = more ? next_row(P, cur, core, ncores, is_long, lane, bad, t) : (t = -1, -1);
             }
@@ -590,7 +592,7 @@ __device__ __forceinline__ void core_updates(const UpdateParams &P, CoreHdr &H, 
 // A block of P.wpb warps: single-warp cores in blocks [0, short_blocks),
 // multi-warp cores of P.group warps after.  `block` counts within the
 // problem's blocks.
-template <typename T, typename I, bool kDense, int kN>
+template <typename T, typename I, bool kDense, int kN, bool kAhead>
 __device__ __forceinline__ void run_block(const UpdateParams &P, unsigned char *smem, int block) {
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const bool is_long = block >= P.short_blocks;
@@ -610,13 +612,13 @@ __device__ __forceinline__ void run_block(const UpdateParams &P, unsigned char *
     __syncthreads();
     if (wib >= cpb * G || core >= ncores) return;  // whole cores leave together
     const int uid = is_long ? P.short_cores + core : core;
-    core_updates<T, I, kDense, kN>(P, H, ring + kCoreHdrBytes, G, w, lane, core, ncores, uid, is_long, 1 + cib);
+    core_updates<T, I, kDense, kN, kAhead>(P, H, ring + kCoreHdrBytes, G, w, lane, core, ncores, uid, is_long, 1 + cib);
 }
 
-template <typename T, typename I, bool kDense>
+template <typename T, typename I, bool kDense, bool kAhead>
 __global__ void __launch_bounds__(kUpdateBlock) update_kernel(const UpdateParams P) {
     extern __shared__ __align__(128) unsigned char smem[];
-    run_block<T, I, kDense, kSlots>(P, smem, (int)blockIdx.x);
+    run_block<T, I, kDense, kSlots, kAhead>(P, smem, (int)blockIdx.x);
 }
 
 // Many independent problems in one launch: block b serves instance
@@ -639,7 +641,7 @@ __global__ void __launch_bounds__(kBatchBlock) batch_update_kernel(const UpdateP
     }
     __syncthreads();
     if (sp.count <= 0) return;
-    run_block<T, I, kDense, kSlots>(sp, smem, (int)blockIdx.x - s_first);
+    run_block<T, I, kDense, kSlots, false>(sp, smem, (int)blockIdx.x - s_first);
 }
 
 // Dynamic shared memory beyond 48 KB must be allowed per kernel.
@@ -651,12 +653,15 @@ struct UpdateLaunch {
     const UpdateParams &p;
     int grid;
     cudaStream_t s;
-    template <typename T, typename I, bool kDense> cudaError_t run() const {
+    template <typename T, typename I, bool kDense, bool kAhead> cudaError_t go() const {
         const size_t smem = update_smem_bytes(p.wpb);
-        const cudaError_t e = allow_smem(update_kernel<T, I, kDense>, smem);
+        const cudaError_t e = allow_smem(update_kernel<T, I, kDense, kAhead>, smem);
         if (e != cudaSuccess) return e;
-        update_kernel<T, I, kDense><<<grid, 32 * p.wpb, smem, s>>>(p);
+        update_kernel<T, I, kDense, kAhead><<<grid, 32 * p.wpb, smem, s>>>(p);
         return cudaGetLastError();
+    }
+    template <typename T, typename I, bool kDense> cudaError_t run() const {
+        return p.draw_ahead ? go<T, I, kDense, true>() : go<T, I, kDense, false>();
     }
 };
 
@@ -697,12 +702,18 @@ struct UpdateOccupancy {
             if (e == cudaSuccess)
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_update_kernel<T, I, kDense>, kBatchBlock,
                                                                   smem);
-        } else {
+        } else {  // the smaller of the two draw placements' figures
             const size_t smem = update_smem_bytes(kUpdateBlock / 32);
-            e = allow_smem(update_kernel<T, I, kDense>, smem);
+            int nb2 = 0;
+            e = allow_smem(update_kernel<T, I, kDense, false>, smem);
+            if (e == cudaSuccess) e = allow_smem(update_kernel<T, I, kDense, true>, smem);
             if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, I, kDense>, kUpdateBlock,
-                                                                  smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, update_kernel<T, I, kDense, false>,
+                                                                  kUpdateBlock, smem);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, update_kernel<T, I, kDense, true>,
+                                                                  kUpdateBlock, smem);
+            nb = std::min(nb, nb2);
         }
         return e == cudaSuccess && nb > 0 ? nb : 1;
     }
