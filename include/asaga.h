@@ -274,7 +274,8 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     of the nonzeros), each timed over two epochs after one untimed; the
  *     two fastest that beat single warps by 3% run a race trial in turn,
  *     and the first whose predicted time beats the winner's by 3% is kept;
- *  6. the draw placement at the winner (asaga_set_draw_ahead): two trials
+ *  6. the draw placement at the winner (asaga_set_draw_ahead), where the
+ *     warps are at most n/256: two trials
  *     of twice the race length with the next row drawn inside the updates'
  *     windows; kept if both bring |grad f|^2 down by 1e10 and the slower
  *     one's update time to that level beats the winner's prediction by 3%

@@ -1471,8 +1471,11 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     //    downward trend (measured: RCV1-shaped rows at the tuned 512 warps),
     //    so a trend is not enough: each of two trials of twice the race
     //    length must reach the prediction level itself, and the slower must
-    //    beat the winner by 3%
-    if (std::isfinite(best_ms)) {
+    //    beat the winner by 3%.  Only where the overlap stays far below n
+    //    (W <= n/256), as for the larger step of step 3: on an instance of
+    //    55 k rows at 431 warps the trials passed and the run then stalled
+    //    at 2e-4 for 3000 epochs.
+    if (std::isfinite(best_ms) && (int64_t)best_w * 256 <= c->n) {
         c->draw_ahead = 1;
         double worst = 0;
         for (int trial = 0; trial < 2 && std::isfinite(worst); ++trial) {
