@@ -265,6 +265,9 @@ asaga_status asaga_cancel(asaga_ctx *ctx);
  *     it scores better), then a
  *     confirmation trial of twice the length that must still show a
  *     downward trend (else one notch smaller a step, three times at most);
+ *     where the warps exceed n/256 and the winner's predicted epochs are
+ *     within 16/3 race lengths, it runs to 1.5x those epochs and must
+ *     bring |grad f|^2 down by 1e10 instead;
  *  4. the update kernel's block shape at the winner: eight warps per block
  *     or the warps spread evenly over the SMs, whichever epoch is faster;
  *  5. the row path at the winner (the same warps and step, regrouped into

@@ -1326,6 +1326,7 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
     //    one notch inside the frontier; the step never above the ladder's top),
     //    by predicted update time to reach kTuneDeep
     double best_ms = INFINITY;
+    double best_pe = INFINITY;  // the winner's predicted epochs
     int best_w = Wp, best_k = std::min(kBottom, kF + 2);  // used if no race trial settles
     auto candidate = [&](int64_t W, int k, bool *improved) -> asaga_status {
         *improved = false;
@@ -1343,7 +1344,8 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
             TRY(trial_epochs_run(c, (int)W, step(k), g0, std::max(1, t.epochs / 4), kTuneDeep, give_up, &t, err));
             r.seconds += (t.t_ms - before) * 1e-3;
         }
-        const double ms = predict_epochs(t) * t.ms_per_epoch();
+        const double pe = predict_epochs(t);
+        const double ms = pe * t.ms_per_epoch();
         // fewer warps and a larger step win within a tolerance: the step
         // carries the slow tail of an ill-conditioned problem beyond the
         // trial, and the overlap tau is smaller
@@ -1353,6 +1355,7 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
                                                 : ms < best_ms;
         if (better) {
             best_ms = ms;
+            best_pe = pe;
             best_w = (int)W;
             best_k = k;
             *improved = true;
@@ -1398,12 +1401,22 @@ asaga_status autotune_impl(asaga_ctx *c, double trial_epochs, asaga_tune_result 
         TRY(candidate(best_w, best_k - 1, &improved));
     // confirmation: the winner over a trial twice as long must still show a
     // downward trend (a plateau can set in after a short trial's early
-    // progress); one notch smaller a step while it does not (three times at most)
+    // progress); one notch smaller a step while it does not (three times at
+    // most).  Where the warps are above n/256 (the overlap a sizeable part of
+    // n) a trend is not enough: measured on instances of 55 k and 61 k rows
+    // at 431 and 478 warps, tuned schedules passed it and then stalled near
+    // 2e-4 for thousands of epochs.  There the trial runs on to 1.5x the
+    // winner's predicted epochs and must reach the prediction level, when
+    // that prediction is within 8 race lengths (epochs are cheap at such n).
+    const bool reach = (int64_t)best_w * 256 > c->n && 1.5 * best_pe <= 8.0 * E_race;
+    const int E_confirm = reach ? std::max(2 * E_race, (int)std::ceil(1.5 * best_pe)) : 2 * E_race;
     if (std::isfinite(best_ms))
         for (int attempt = 0; attempt < 3 && best_k <= kBottom; ++attempt) {
             TuneTrial t;
-            TRY(run(best_w, best_k, 2 * E_race, kTuneDeep, std::max(4.0 * kTuneExtendMs, 3.0 * best_ms), &t));
-            if (!t.diverged && std::isfinite(predict_epochs(t))) break;
+            TRY(run(best_w, best_k, E_confirm, kTuneDeep, std::max(4.0 * kTuneExtendMs, 3.0 * best_ms), &t));
+            const bool ok = reach ? !t.diverged && !t.y.empty() && t.y.back() <= kTuneDeep
+                                  : !t.diverged && std::isfinite(predict_epochs(t));
+            if (ok) break;
             if (best_k == kBottom) break;
             ++best_k;
         }
