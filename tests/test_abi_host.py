@@ -162,6 +162,12 @@ def test_set_schedule_needs_a_context(lib):
     assert asaga.load().asaga_set_schedule(None, 4, 0.1, 0) == asaga.EINVAL
 
 
+def test_row_path_and_draw_placement_need_a_context(lib):
+    L = asaga.load()
+    assert L.asaga_set_row_path(None, 0, 2) == asaga.EINVAL
+    assert L.asaga_set_draw_ahead(None, 1) == asaga.EINVAL
+
+
 def test_line_probe_arguments_are_checked_before_any_cuda_call(lib):
     import ctypes
 
